@@ -1,0 +1,110 @@
+"""Seeded synthetic workloads for the FMM-preconditioned Helmholtz solver.
+
+This module only draws random numbers and names problem sizes.  It holds none
+of the method's arithmetic (no Green's function, no expansion, no stencil), so
+both the CUDA path and the independent CPU oracle may take their inputs from it.
+
+Problem (paper Sec. 2, Eq. (helm), Dirichlet variant of Sec. 6/7): the 3D
+Helmholtz equation -Lap u - k^2 u = f on the unit cube, u = 0 on the boundary,
+discretised on the n^3 interior nodes x = (i, j, l) h, h = 1/(n+1),
+i, j, l = 1..n.  Vectors over the interior are in lexicographic order with the
+x index fastest.
+
+The paper measures on 2D MATLAB model problems and on 3D problems whose data
+it does not print; these synthetic right-hand sides stand in for them.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# name -> workload description.  k is the wavenumber, p the expansion order
+# (degrees 0..p-1), leaf the target number of volume nodes per leaf, theta the
+# multipole acceptance parameter, restart the GMRES restart length m.
+WORKLOADS = {
+    # plain FP64 method, small enough for the oracle
+    "helmholtz_n16_k4_p4": dict(n=16, k=4.0, p=4, leaf=32, theta=0.4, restart=30,
+                                rhs="uniform_real", seed=1),
+    # plain method vs FP32 form
+    "helmholtz_n64_k16_p6": dict(n=64, k=16.0, p=6, leaf=64, theta=0.4, restart=50,
+                                 rhs="gaussians", seed=2),
+    # FP32 form at scale
+    "helmholtz_n128_k32_p8": dict(n=128, k=32.0, p=8, leaf=64, theta=0.35, restart=50,
+                                  rhs="complex_normal", seed=3),
+    # free-space volume FMM for the differentiable form
+    "fmm_n64_k12_p6": dict(n=64, k=12.0, p=6, leaf=64, theta=0.4, restart=50,
+                           rhs="complex_normal_unit", seed=5),
+}
+
+
+def node_coords(n: int) -> np.ndarray:
+    """Interior node coordinates, shape (n^3, 3), lexicographic with x fastest."""
+    h = 1.0 / (n + 1)
+    i = np.arange(1, n + 1, dtype=np.float64) * h
+    z, y, x = np.meshgrid(i, i, i, indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+
+def rhs(kind: str, n: int, seed: int) -> np.ndarray:
+    """Right-hand side f on the interior nodes as complex128, shape (n^3,)."""
+    rng = np.random.default_rng(seed)
+    N = n ** 3
+    if kind == "uniform_real":
+        return rng.uniform(-1.0, 1.0, N).astype(np.complex128)
+    if kind == "gaussians":
+        # 8 Gaussian sources, sigma 0.05, unit amplitude, centres uniform in
+        # [0.2, 0.8]^3, over a uniform[-1, 1] background.
+        centres = rng.uniform(0.2, 0.8, (8, 3))
+        background = rng.uniform(-1.0, 1.0, N)
+        x = node_coords(n)
+        f = background.copy()
+        for c in centres:
+            d2 = np.sum((x - c) ** 2, axis=1)
+            f += np.exp(-d2 / (2.0 * 0.05 ** 2))
+        return f.astype(np.complex128)
+    if kind == "complex_normal":
+        # real and imaginary parts each N(0, 1)
+        re = rng.standard_normal(N)
+        im = rng.standard_normal(N)
+        return re + 1j * im
+    if kind == "complex_normal_unit":
+        # circular complex normal with E|z|^2 = 1
+        re = rng.standard_normal(N)
+        im = rng.standard_normal(N)
+        return (re + 1j * im) / np.sqrt(2.0)
+    raise ValueError(f"unknown rhs kind {kind!r}")
+
+
+def workload_rhs(name: str) -> np.ndarray:
+    w = WORKLOADS[name]
+    return rhs(w["rhs"], w["n"], w["seed"])
+
+
+def complex_normal(shape, seed: int) -> np.ndarray:
+    """Circular complex normal samples (E|z|^2 = 1), complex128."""
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal(shape)
+    im = rng.standard_normal(shape)
+    return (re + 1j * im) / np.sqrt(2.0)
+
+
+def uniform_points(count: int, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """Points uniform in [lo, hi)^3, shape (count, 3), float64."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, (count, 3))
+
+
+def batched_problems(count: int = 48, seed: int = 4):
+    """Independent solves of uneven size: n from {24,32,48,64,96}, k uniform in
+    [4, min(32, 2 pi (n+1) / 8)] (at least 8 points per wavelength), p in {4, 6}.
+    Each solve s gets f ~ uniform[-1, 1] from seed 1000 + s."""
+    rng = np.random.default_rng(seed)
+    sizes = np.array([24, 32, 48, 64, 96])
+    out = []
+    for s in range(count):
+        n = int(rng.choice(sizes))
+        kmax = min(32.0, 2.0 * np.pi * (n + 1) / 8.0)
+        k = float(rng.uniform(4.0, kmax))
+        p = int(rng.choice([4, 6]))
+        out.append(dict(n=n, k=k, p=p, leaf=64, theta=0.4, restart=50,
+                        rhs="uniform_real", seed=1000 + s))
+    return out
