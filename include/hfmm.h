@@ -1,0 +1,207 @@
+/*
+ * hfmm.h -- C ABI of the GB300 (sm_103a) FMM-preconditioned Helmholtz solver.
+ *
+ * Method: Ibeid, Yokota, Keyes, "A Matrix-free Preconditioner for the
+ * Helmholtz Equation based on the Fast Multipole Method".  The library solves
+ * the 7-point finite-difference discretisation of -Lap u - k^2 u = f on the
+ * unit cube with u = 0 on the boundary (Sec. 2, Eq. (helm), Dirichlet case of
+ * Sec. 6/7) by right-preconditioned GMRES (Sec. 3-4); the preconditioner is
+ * the BEM-coupled FMM of Sec. 5 (FMM flow of Sec. 5.1.2, boundary equation
+ * Eq. (ubound), interior representation Eq. (uinter)).
+ *
+ * Conventions for every entry point
+ *  - Pointers named d_* are DEVICE memory owned by the caller; the library
+ *    never frees them and keeps no reference after the call returns.
+ *  - Complex vectors are interleaved (re, im) float64 pairs (the layout of
+ *    complex128 / cuDoubleComplex), whatever the internal precision.
+ *  - Interior-node vectors have n^3 entries, node (i, j, l) h with h = 1/(n+1)
+ *    at index (i-1) + n (j-1) + n^2 (l-1) (x fastest).
+ *  - Boundary vectors have 6 n^2 entries, one constant element (panel) per
+ *    boundary grid node off the cube's edges, faces in the order x=0, x=1,
+ *    y=0, y=1, z=0, z=1, first free coordinate fastest within a face.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    stream-ordered; entry points that must read a scalar back (GMRES) block
+ *    the host on that stream.
+ *  - Every call returns an int status (HFMM_OK = 0, negative on error) and
+ *    throws nothing.  On an argument error nothing is written.
+ *  - The fmm_tree handle owns all its device workspace; it is not thread
+ *    safe: calls on one handle must be serialised by the caller.
+ */
+#ifndef HFMM_H
+#define HFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HFMM_OK                 0
+#define HFMM_ERR_INVALID_ARG   -1
+#define HFMM_ERR_CUDA          -2
+#define HFMM_ERR_NOMEM         -3
+#define HFMM_ERR_NONFINITE     -4
+#define HFMM_ERR_NOT_CONVERGED -5
+#define HFMM_ERR_TIMEOUT       -6
+#define HFMM_ERR_UNSUPPORTED   -7
+
+/* internal arithmetic of the FMM stages (Krylov arithmetic is always FP64) */
+#define HFMM_FP64 0
+#define HFMM_FP32 1
+
+/* point sets */
+#define HFMM_SET_VOL 1   /* interior nodes (volume term of Eq. (uinter)) */
+#define HFMM_SET_BND 2   /* boundary elements (boundary terms)           */
+
+/* fmm_apply modes */
+#define HFMM_FWD 0       /* phi = G~ q                                   */
+
+typedef struct hfmm_params {
+    int p;            /* expansion order: degrees 0..p-1 (1 <= p <= 16)  */
+    double theta;     /* multipole acceptance parameter, 0 < theta <= 0.55:
+                         same-level cells at centre distance d are far iff
+                         theta * d > cell width                          */
+    int leaf_size;    /* target interior nodes per leaf; the tree is uniform
+                         of depth L = max(2, ceil(log8(n_vol / leaf_size)))  */
+    double k;         /* wavenumber, k >= 0                              */
+    int precision;    /* HFMM_FP64 or HFMM_FP32                          */
+} hfmm_params;
+
+typedef struct hfmm_gmres_params {
+    int restart_m;     /* outer GMRES restart length m (1..200)            */
+    double rtol;       /* stop when |g_{j+1}| < rtol ||b|| (Sec. 6: 1e-6)  */
+    int maxit;         /* cap on preconditioner applications (0: 20 m)     */
+    double inner_rtol; /* tolerance of the inner boundary solve V q = -g   */
+    int inner_maxit;   /* cap on inner iterations per preconditioner apply */
+    int inner_m;       /* restart length of the inner GMRES                */
+} hfmm_gmres_params;
+
+typedef struct hfmm_gmres_info {
+    int iters;             /* preconditioner applications (all restarts)  */
+    int restarts;
+    int inner_iters_total; /* inner GMRES iterations over all applies     */
+    int status;            /* HFMM_OK or HFMM_ERR_NOT_CONVERGED           */
+    double relres_est;     /* |g_{j+1}| / ||b|| at exit                   */
+    double relres_true;    /* ||b - A x|| / ||b|| at exit                 */
+    double* history;       /* optional host array (caller-owned) of length
+                              history_len: relres_est per iteration       */
+    int history_len;
+} hfmm_gmres_info;
+
+typedef struct hfmm_stats {
+    int L;                 /* tree depth                                   */
+    int p;
+    int64_t n_vol, n_bnd;
+    int64_t leaves;
+    int64_t m2l_pairs;     /* far-field cell pairs over all levels (volume+boundary sets) */
+    int64_t p2p_pairs;     /* near-field point pairs, all points as sources and targets */
+    int64_t device_bytes;  /* device memory held by the handle              */
+    double ms_last_apply;  /* CUDA-event time of the last fmm_apply/precond */
+} hfmm_stats;
+
+typedef struct fmm_tree fmm_tree;
+
+/* Text for a status code (static storage). */
+const char* hfmm_error_string(int status);
+
+/*
+ * fmm_build_tree -- Sec. 5.1.1 (octree decomposition), Sec. 5.3 (constant
+ * boundary elements), Sec. 7 (p, theta).
+ *
+ * Builds the uniform Morton-ordered octree over the interior nodes and the
+ * boundary panels of the n^3 grid, the near (P2P) and far (M2L) interaction
+ * lists, every translation operator for wavenumber k, and the singular self
+ * terms of cells and panels.  All of it runs in device kernels on `stream`.
+ *
+ *   n          interior nodes per axis (n >= 2); h = 1/(n+1)
+ *   d_vol_xyz  NULL: the n^3 lattice nodes.  Otherwise n_vol points (AoS
+ *              x,y,z float64, device) in [0,1]^3 that replace them; the
+ *              self terms are then zero (no cell volume is implied).
+ *   n_vol      number of interior points (n^3 when d_vol_xyz is NULL)
+ *   d_bnd_xyz  NULL: the 6 n^2 lattice panels.  Otherwise n_bnd points.
+ *   n_bnd      number of boundary points (6 n^2 when d_bnd_xyz is NULL;
+ *              0 allowed with explicit points)
+ *   params     see hfmm_params
+ *   out        receives the handle (NULL on error)
+ * Errors: INVALID_ARG (sizes, p, theta, k, precision), NOMEM, CUDA.
+ */
+int fmm_build_tree(int n, const double* d_vol_xyz, int64_t n_vol,
+                   const double* d_bnd_xyz, int64_t n_bnd,
+                   const hfmm_params* params, void* stream, fmm_tree** out);
+
+/* Releases the handle and all its device memory (NULL is a no-op). */
+void fmm_destroy_tree(fmm_tree* tree);
+
+/*
+ * fmm_apply -- Sec. 5.1 N-body sum with the 3D Helmholtz kernel of Sec. 5.2,
+ * G(x, y) = exp(i k |x-y|) / (4 pi |x-y|), by the FMM of Sec. 5.1.2.
+ *
+ *   phi_i = sum_{j in src_set, j != i} q_j G(x_i, x_j) + [i in src_set] s_i q_i
+ *
+ * for every target i in tgt_set, where s_i is the self coefficient: the
+ * integral of G over the point's own cell divided by h^3 (interior node) or
+ * over its own panel divided by h^2 (boundary element); zero for explicit
+ * points.  Weights are used as given (no quadrature weight is applied).
+ *
+ *   src_set, tgt_set  non-zero OR of HFMM_SET_VOL / HFMM_SET_BND
+ *   d_q_vol, d_q_bnd  source weights (complex128) per set; a set not in
+ *                     src_set may be NULL
+ *   d_phi_vol, d_phi_bnd  outputs (complex128) per set in tgt_set
+ *                     (overwritten); a set not in tgt_set may be NULL
+ *   mode              HFMM_FWD
+ * Errors: INVALID_ARG, CUDA.
+ */
+int fmm_apply(fmm_tree* tree, int src_set, int tgt_set,
+              const void* d_q_vol, const void* d_q_bnd,
+              void* d_phi_vol, void* d_phi_bnd, int mode, void* stream);
+
+/*
+ * fmm_precond_apply -- z = M^-1 r, the BEM-coupled FMM preconditioner of
+ * Sec. 5.2-5.3 with homogeneous Dirichlet data:
+ *   w = h^3 r;  g = G_{Gamma,Omega} w                         (Pass A)
+ *   solve V q = -g, V = h^2 G_{Gamma,Gamma} + self terms      (inner GMRES,
+ *                                                              Pass B per step)
+ *   z = G_{Omega,Omega} w + G_{Omega,Gamma} (h^2 q) + s_Omega r (Pass C)
+ * Requires a lattice tree (d_vol_xyz == NULL at build).
+ *   d_r, d_z       n^3 complex128 (device); d_z is overwritten
+ *   inner_rtol     relative tolerance of the inner solve (> 0)
+ *   inner_maxit    inner iteration cap (>= 1); inner_m its restart length
+ *   inner_iters    optional host int receiving the inner iteration count
+ * The inner solve stopping at inner_maxit is not an error.
+ * Errors: INVALID_ARG, UNSUPPORTED (explicit points), CUDA.
+ */
+int fmm_precond_apply(fmm_tree* tree, const void* d_r, void* d_z,
+                      double inner_rtol, int inner_maxit, int inner_m,
+                      int* inner_iters, void* stream);
+
+/*
+ * hfmm_fdm_apply -- the 7-point operator of Sec. 2 (reading: -Lap - k^2):
+ *   (A u)_i = (6 u_i - sum of the six neighbours) / h^2 - k^2 u_i,
+ * neighbours outside the grid being zero.  d_u, d_out: n^3 complex128.
+ */
+int hfmm_fdm_apply(fmm_tree* tree, const void* d_u, void* d_out, void* stream);
+
+/*
+ * gmres_solve -- Sec. 3-4, Sec. 6: flexible right-preconditioned restarted
+ * GMRES(m) for A x = b with A the 7-point operator of the tree's (n, k) and
+ * M^-1 = fmm_precond_apply.  Classical Gram-Schmidt with reorthogonalisation,
+ * complex Givens rotations, FP64 throughout the Krylov arithmetic.
+ *   d_b     n^3 complex128 right-hand side
+ *   d_x     in: initial guess x0; out: solution (written also when the
+ *           status is NOT_CONVERGED)
+ *   info    host struct, filled on return (history optional)
+ * Returns HFMM_OK when converged, HFMM_ERR_NOT_CONVERGED after maxit
+ * applications, or another error.
+ */
+int gmres_solve(fmm_tree* tree, const void* d_b, void* d_x,
+                const hfmm_gmres_params* gp, hfmm_gmres_info* info, void* stream);
+
+/* Sizes and counters of a built tree. */
+int fmm_get_stats(const fmm_tree* tree, hfmm_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFMM_H */

@@ -1,0 +1,309 @@
+// The C ABI declared in include/hfmm.h: handle life cycle, argument checks,
+// the FMM apply, the BEM-coupled preconditioner (Sec. 5.2-5.3) and the outer
+// preconditioned GMRES (Sec. 3-4, Sec. 6).
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "krylov.cuh"
+#include "tree.cuh"
+
+struct fmm_tree_ext {
+  GmresWork inner;   // boundary solve V q = -g
+  GmresWork outer;   // A x = b
+};
+
+namespace {
+
+// theta as a rational num/den with den <= 1000 (exact for decimal inputs)
+void theta_rational(double th, int64_t& num, int64_t& den) {
+  for (int64_t d = 1; d <= 1000; ++d) {
+    double n = th * d;
+    int64_t r = (int64_t)llround(n);
+    if (r > 0 && fabs(n - r) < 1e-9 * d) {
+      num = r;
+      den = d;
+      return;
+    }
+  }
+  den = 1000;
+  num = (int64_t)llround(th * 1000);
+}
+
+void release(fmm_tree* t) {
+  if (!t) return;
+  for (auto& b : t->bufs) cudaFree(b.ptr);
+  t->bufs.clear();
+  if (t->ev0) cudaEventDestroy(t->ev0);
+  if (t->ev1) cudaEventDestroy(t->ev1);
+}
+
+fmm_tree_ext* ext_of(fmm_tree* t) { return t->ext; }
+
+}  // namespace
+
+int tree_alloc(fmm_tree* t, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return HFMM_ERR_NOMEM;
+  }
+  t->bufs.push_back({*ptr, bytes});
+  t->device_bytes += (int64_t)bytes;
+  return HFMM_OK;
+}
+
+extern "C" const char* hfmm_error_string(int status) {
+  switch (status) {
+    case HFMM_OK: return "ok";
+    case HFMM_ERR_INVALID_ARG: return "invalid argument";
+    case HFMM_ERR_CUDA: return "CUDA error";
+    case HFMM_ERR_NOMEM: return "out of device memory";
+    case HFMM_ERR_NONFINITE: return "non-finite value encountered";
+    case HFMM_ERR_NOT_CONVERGED: return "iteration did not converge";
+    case HFMM_ERR_TIMEOUT: return "timeout";
+    case HFMM_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cudaStream_t s) {
+  const int P = t->P;
+  // level offsets of the per-cell arrays
+  int64_t off = 0;
+  for (int l = 0; l <= t->L; ++l) {
+    t->level_off[l] = off;
+    off += (int64_t)1 << (3 * l);
+  }
+  t->level_off[t->L + 1] = off;
+  t->total_cells = off;
+  const int64_t nleaf = (int64_t)1 << (3 * t->L);
+  const int64_t N = t->n_pts;
+  HFMM_TRY(tree_alloc_t(t, &t->xyz, 3 * N));
+  HFMM_TRY(tree_alloc_t(t, &t->xyz32, 4 * N));
+  HFMM_TRY(tree_alloc_t(t, &t->orig, N));
+  HFMM_TRY(tree_alloc_t(t, &t->pos_of, N));
+  HFMM_TRY(tree_alloc_t(t, &t->leaf_start, nleaf + 1));
+  HFMM_TRY(tree_alloc_t(t, &t->leaf_mid, nleaf));
+  HFMM_TRY(tree_alloc_t(t, &t->flags, t->total_cells));
+  const size_t csz = t->precision == HFMM_FP32 ? sizeof(float2) : sizeof(double2);
+  HFMM_TRY(tree_alloc(t, &t->M, csz * t->total_cells * P));
+  HFMM_TRY(tree_alloc(t, &t->Lc, csz * t->total_cells * P));
+  HFMM_TRY(tree_alloc(t, &t->qs, csz * N));
+  HFMM_TRY(tree_alloc(t, &t->phis, csz * N));
+  HFMM_TRY(tree_alloc_t(t, &t->g_bnd, t->n_bnd + 1));
+  HFMM_TRY(tree_alloc_t(t, &t->q_bnd, t->n_bnd + 1));
+  HFMM_CUDA_TRY(cudaMemsetAsync(t->M, 0, csz * t->total_cells * P, s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(t->Lc, 0, csz * t->total_cells * P, s));
+  HFMM_TRY(build_geometry_and_sort(t, d_vol, d_bnd, s));
+  HFMM_TRY(build_lists(t, s));
+  HFMM_TRY(build_self_terms(t, s));
+  HFMM_TRY(build_operators(t, s));
+  HFMM_CUDA_TRY(cudaEventCreate(&t->ev0));
+  HFMM_CUDA_TRY(cudaEventCreate(&t->ev1));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  return HFMM_OK;
+}
+
+extern "C" int fmm_build_tree(int n, const double* d_vol_xyz, int64_t n_vol, const double* d_bnd_xyz,
+                              int64_t n_bnd, const hfmm_params* params, void* stream,
+                              fmm_tree** out) {
+  if (!out) return HFMM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!params) return HFMM_ERR_INVALID_ARG;
+  const hfmm_params& pr = *params;
+  if (pr.p < 1 || pr.p > HFMM_MAX_P) return HFMM_ERR_INVALID_ARG;
+  if (!(pr.theta > 0.0 && pr.theta <= 0.55)) return HFMM_ERR_INVALID_ARG;
+  if (pr.leaf_size < 1) return HFMM_ERR_INVALID_ARG;
+  if (!(pr.k > 0.0) || !std::isfinite(pr.k)) return HFMM_ERR_INVALID_ARG;
+  if (pr.precision != HFMM_FP64 && pr.precision != HFMM_FP32) return HFMM_ERR_INVALID_ARG;
+  const bool lattice = d_vol_xyz == nullptr && d_bnd_xyz == nullptr;
+  if (lattice) {
+    if (n < 2 || n > 1024) return HFMM_ERR_INVALID_ARG;
+    n_vol = (int64_t)n * n * n;
+    n_bnd = 6 * (int64_t)n * n;
+  } else {
+    if (d_vol_xyz == nullptr || n_vol < 1 || n_bnd < 0 || (n_bnd > 0 && !d_bnd_xyz))
+      return HFMM_ERR_INVALID_ARG;
+  }
+  if (n_vol + n_bnd > ((int64_t)1 << 30)) return HFMM_ERR_INVALID_ARG;
+  fmm_tree* t = new (std::nothrow) fmm_tree();
+  if (!t) return HFMM_ERR_NOMEM;
+  t->ext = new (std::nothrow) fmm_tree_ext();
+  if (!t->ext) {
+    delete t;
+    return HFMM_ERR_NOMEM;
+  }
+  t->n = lattice ? n : 0;
+  t->lattice = lattice ? 1 : 0;
+  t->n_vol = n_vol;
+  t->n_bnd = n_bnd;
+  t->n_pts = n_vol + n_bnd;
+  t->h = lattice ? 1.0 / (n + 1) : 0.0;
+  t->k = pr.k;
+  t->p = pr.p;
+  t->P = pr.p * pr.p;
+  t->precision = pr.precision;
+  t->leaf_size = pr.leaf_size;
+  t->theta = pr.theta;
+  theta_rational(pr.theta, t->th_num, t->th_den);
+  int L = 2;
+  while ((int64_t)pr.leaf_size * ((int64_t)1 << (3 * L)) < n_vol) ++L;
+  if (L > HFMM_MAX_LEVEL - 1) {
+    delete t->ext;
+    delete t;
+    return HFMM_ERR_UNSUPPORTED;
+  }
+  t->L = L;
+  t->nlv = 1 << L;
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = build_impl(t, d_vol_xyz, d_bnd_xyz, s);
+  if (st != HFMM_OK) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    release(t);
+    delete t->ext;
+    delete t;
+    return st;
+  }
+  *out = t;
+  return HFMM_OK;
+}
+
+extern "C" void fmm_destroy_tree(fmm_tree* tree) {
+  if (!tree) return;
+  cudaDeviceSynchronize();
+  fmm_tree_ext* e = ext_of(tree);
+  gmres_work_free(e->inner);
+  gmres_work_free(e->outer);
+  release(tree);
+  delete e;
+  delete tree;
+}
+
+extern "C" int fmm_apply(fmm_tree* t, int src_set, int tgt_set, const void* d_q_vol, const void* d_q_bnd,
+                         void* d_phi_vol, void* d_phi_bnd, int mode, void* stream) {
+  if (!t) return HFMM_ERR_INVALID_ARG;
+  const int all = HFMM_SET_VOL | HFMM_SET_BND;
+  if (src_set <= 0 || (src_set & ~all) || tgt_set <= 0 || (tgt_set & ~all)) return HFMM_ERR_INVALID_ARG;
+  if (mode != HFMM_FWD) return HFMM_ERR_UNSUPPORTED;
+  if ((src_set & HFMM_SET_VOL) && !d_q_vol) return HFMM_ERR_INVALID_ARG;
+  if ((src_set & HFMM_SET_BND) && t->n_bnd > 0 && !d_q_bnd) return HFMM_ERR_INVALID_ARG;
+  if ((tgt_set & HFMM_SET_VOL) && !d_phi_vol) return HFMM_ERR_INVALID_ARG;
+  if ((tgt_set & HFMM_SET_BND) && t->n_bnd > 0 && !d_phi_bnd) return HFMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  HFMM_CUDA_TRY(cudaEventRecord(t->ev0, s));
+  HFMM_TRY(fmm_gather(t, src_set, (const double2*)d_q_vol, 1.0, (const double2*)d_q_bnd, 1.0, s));
+  HFMM_TRY(fmm_core(t, src_set, tgt_set, s));
+  HFMM_TRY(fmm_scatter(t, tgt_set, (double2*)d_phi_vol, (double2*)d_phi_bnd, s));
+  HFMM_CUDA_TRY(cudaEventRecord(t->ev1, s));
+  return HFMM_OK;
+}
+
+// z = M^-1 r (Sec. 5.2-5.3, homogeneous Dirichlet data)
+static int precond_impl(fmm_tree* t, const double2* r, double2* z, double inner_rtol, int inner_maxit,
+                        int inner_m, int* inner_iters, cudaStream_t s) {
+  const double h = t->h, h2 = h * h, h3 = h2 * h;
+  // Pass A: g = G_{Gamma,Omega} (h^3 r)
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL, r, h3, nullptr, 0.0, s));
+  HFMM_TRY(fmm_core(t, HFMM_SET_VOL, HFMM_SET_BND, s));
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, t->g_bnd, s));
+  // inner solve V q = -g; V x = h^2 G_{Gamma,Gamma} x + s_Gamma x (Pass B)
+  fmm_tree_ext* e = ext_of(t);
+  HFMM_TRY(gmres_work_reserve(e->inner, t->n_bnd, inner_m, false));
+  // rhs = -g, computed in place with a scaled gather/scatter-free kernel: reuse
+  // GMRES on the negated operator instead: solve (-V) q = g
+  DevOp negV = [t, h2, s](const double2* in, double2* out) -> int {
+    HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, in, -h2, s));
+    HFMM_TRY(fmm_core(t, HFMM_SET_BND, HFMM_SET_BND, s));
+    return fmm_scatter(t, HFMM_SET_BND, nullptr, out, s);
+  };
+  HFMM_CUDA_TRY(cudaMemsetAsync(t->q_bnd, 0, sizeof(double2) * t->n_bnd, s));
+  GmresResult ir;
+  HFMM_TRY(gmres_run(e->inner, negV, nullptr, t->g_bnd, t->q_bnd, inner_m, inner_rtol, inner_maxit,
+                     true, false, &ir, nullptr, 0, s));
+  if (inner_iters) *inner_iters = ir.iters;
+  // Pass C: z = G_{Omega,Omega} (h^3 r) + G_{Omega,Gamma} (h^2 q) + s_Omega r
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, r, h3, t->q_bnd, h2, s));
+  HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, s));
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_VOL, z, nullptr, s));
+  return HFMM_OK;
+}
+
+extern "C" int fmm_precond_apply(fmm_tree* t, const void* d_r, void* d_z, double inner_rtol,
+                                 int inner_maxit, int inner_m, int* inner_iters, void* stream) {
+  if (!t || !d_r || !d_z) return HFMM_ERR_INVALID_ARG;
+  if (!t->lattice) return HFMM_ERR_UNSUPPORTED;
+  if (!(inner_rtol > 0.0) || inner_maxit < 1 || inner_m < 1 || inner_m > 500) return HFMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  HFMM_CUDA_TRY(cudaEventRecord(t->ev0, s));
+  HFMM_TRY(precond_impl(t, (const double2*)d_r, (double2*)d_z, inner_rtol, inner_maxit, inner_m,
+                        inner_iters, s));
+  HFMM_CUDA_TRY(cudaEventRecord(t->ev1, s));
+  return HFMM_OK;
+}
+
+extern "C" int hfmm_fdm_apply(fmm_tree* t, const void* d_u, void* d_out, void* stream) {
+  if (!t || !d_u || !d_out) return HFMM_ERR_INVALID_ARG;
+  if (!t->lattice) return HFMM_ERR_UNSUPPORTED;
+  return fdm_apply_dev(t->n, t->h, t->k, (const double2*)d_u, (double2*)d_out, (cudaStream_t)stream);
+}
+
+extern "C" int gmres_solve(fmm_tree* t, const void* d_b, void* d_x, const hfmm_gmres_params* gp,
+                           hfmm_gmres_info* info, void* stream) {
+  if (!t || !d_b || !d_x || !gp) return HFMM_ERR_INVALID_ARG;
+  if (!t->lattice) return HFMM_ERR_UNSUPPORTED;
+  if (gp->restart_m < 1 || gp->restart_m > 200 || !(gp->rtol > 0.0) || gp->maxit < 0 ||
+      !(gp->inner_rtol > 0.0) || gp->inner_maxit < 1 || gp->inner_m < 1 || gp->inner_m > 500)
+    return HFMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  fmm_tree_ext* e = ext_of(t);
+  const int64_t N = t->n_vol;
+  HFMM_TRY(gmres_work_reserve(e->outer, N, gp->restart_m, true));
+  DevOp A = [t, s](const double2* in, double2* out) -> int {
+    return fdm_apply_dev(t->n, t->h, t->k, in, out, s);
+  };
+  int inner_total = 0;
+  DevOp M = [t, gp, s, &inner_total](const double2* in, double2* out) -> int {
+    int its = 0;
+    int st = precond_impl(t, in, out, gp->inner_rtol, gp->inner_maxit, gp->inner_m, &its, s);
+    inner_total += its;
+    return st;
+  };
+  const int maxit = gp->maxit > 0 ? gp->maxit : 20 * gp->restart_m;
+  GmresResult R;
+  int st = gmres_run(e->outer, A, &M, (const double2*)d_b, (double2*)d_x, gp->restart_m, gp->rtol, maxit,
+                     false, true, &R, info ? info->history : nullptr, info ? info->history_len : 0, s);
+  if (info) {
+    info->iters = R.iters;
+    info->restarts = R.restarts;
+    info->inner_iters_total = inner_total;
+    info->relres_est = R.relres_est;
+    info->relres_true = R.relres_true;
+    info->status = st != HFMM_OK ? st : (R.converged ? HFMM_OK : HFMM_ERR_NOT_CONVERGED);
+  }
+  if (st != HFMM_OK) return st;
+  return R.converged ? HFMM_OK : HFMM_ERR_NOT_CONVERGED;
+}
+
+extern "C" int fmm_get_stats(const fmm_tree* t, hfmm_stats* st) {
+  if (!t || !st) return HFMM_ERR_INVALID_ARG;
+  st->L = t->L;
+  st->p = t->p;
+  st->n_vol = t->n_vol;
+  st->n_bnd = t->n_bnd;
+  st->leaves = (int64_t)1 << (3 * t->L);
+  st->m2l_pairs = t->m2l_pairs;
+  st->p2p_pairs = t->p2p_pairs;
+  st->device_bytes = t->device_bytes;
+  float ms = 0.f;
+  fmm_tree* tt = const_cast<fmm_tree*>(t);
+  if (tt->ev0 && tt->ev1 && cudaEventElapsedTime(&ms, tt->ev0, tt->ev1) == cudaSuccess)
+    tt->ms_last_apply = ms;
+  else
+    cudaGetLastError();
+  st->ms_last_apply = tt->ms_last_apply;
+  return HFMM_OK;
+}

@@ -1,0 +1,100 @@
+// Shared device helpers: complex arithmetic, Morton codes, error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hfmm.h"
+
+#define HFMM_MAX_P 16
+#define HFMM_MAX_LEVEL 9
+
+// ---------------------------------------------------------------- complex
+
+template <typename T> struct cplx;
+template <> struct cplx<double> { using type = double2; };
+template <> struct cplx<float> { using type = float2; };
+template <typename T> using C = typename cplx<T>::type;
+
+template <typename T>
+__host__ __device__ __forceinline__ C<T> mkc(T re, T im) {
+  C<T> z;
+  z.x = re;
+  z.y = im;
+  return z;
+}
+template <typename T>
+__host__ __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mkc<T>(a.x + b.x, a.y + b.y); }
+template <typename T>
+__host__ __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return mkc<T>(a.x - b.x, a.y - b.y); }
+template <typename T>
+__host__ __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+  return mkc<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__host__ __device__ __forceinline__ C<T> conjc(C<T> a) { return mkc<T>(a.x, -a.y); }
+template <typename T>
+__host__ __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mkc<T>(a.x * s, a.y * s); }
+// acc += a * b
+template <typename T>
+__host__ __device__ __forceinline__ void cfma(C<T>& acc, C<T> a, C<T> b) {
+  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+// acc += conj(a) * b
+template <typename T>
+__host__ __device__ __forceinline__ void cfma_conj(C<T>& acc, C<T> a, C<T> b) {
+  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+}
+
+// ---------------------------------------------------------------- Morton codes
+
+// spread the low 21 bits of v to every third bit
+__host__ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffULL;
+  v = (v | (v << 32)) & 0x1f00000000ffffULL;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+  v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+  v = (v | (v << 2)) & 0x1249249249249249ULL;
+  return v;
+}
+__host__ __device__ __forceinline__ uint64_t compact3(uint64_t v) {
+  v &= 0x1249249249249249ULL;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ULL;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00fULL;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffULL;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffULL;
+  v = (v ^ (v >> 32)) & 0x1fffffULL;
+  return v;
+}
+// bit 0 of each triple = x, bit 1 = y, bit 2 = z
+__host__ __device__ __forceinline__ uint64_t morton_encode(int ix, int iy, int iz) {
+  return spread3((uint64_t)ix) | (spread3((uint64_t)iy) << 1) | (spread3((uint64_t)iz) << 2);
+}
+__host__ __device__ __forceinline__ void morton_decode(uint64_t m, int& ix, int& iy, int& iz) {
+  ix = (int)compact3(m);
+  iy = (int)compact3(m >> 1);
+  iz = (int)compact3(m >> 2);
+}
+
+// ---------------------------------------------------------------- error plumbing
+
+#define HFMM_CUDA_TRY(expr)                              \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return HFMM_ERR_CUDA;         \
+  } while (0)
+
+#define HFMM_TRY(expr)                                   \
+  do {                                                   \
+    int _s = (expr);                                     \
+    if (_s != HFMM_OK) return _s;                        \
+  } while (0)
+
+static inline int hfmm_last_launch() {
+  return cudaGetLastError() == cudaSuccess ? HFMM_OK : HFMM_ERR_CUDA;
+}
+
+static inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }

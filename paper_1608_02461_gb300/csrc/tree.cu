@@ -1,0 +1,460 @@
+// Tree construction on the device (Sec. 5.1.1: recursive subdivision of the
+// cube into eight cells down to a uniform leaf level; Sec. 5.3: constant
+// boundary elements centred at the boundary grid nodes off the edges).
+//
+//  - geometry: interior nodes (i,j,l) h and boundary panels, or caller points
+//  - leaf keys: Morton code of floor(x 2^L) clamped to 2^L - 1
+//  - counting sort into leaf order; inside a leaf, volume points first, then
+//    boundary points, each set by original index (deterministic)
+//  - per-level occupancy flags (bit 0 volume, bit 1 boundary)
+//  - near list and per-parity M2L lists from the acceptance test
+//    theta |d| > 1 (d in cell widths) evaluated in integers
+//  - singular self terms of a cell and of a panel
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "special.cuh"
+#include "tree.cuh"
+
+namespace {
+
+__global__ void k_lattice_points(int n, double h, int64_t n_vol, int64_t n_bnd, double* xyz) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n_vol) {
+    int64_t a = i % n, b = (i / n) % n, c = i / ((int64_t)n * n);
+    xyz[3 * i + 0] = (a + 1) * h;
+    xyz[3 * i + 1] = (b + 1) * h;
+    xyz[3 * i + 2] = (c + 1) * h;
+  } else if (i < n_vol + n_bnd) {
+    int64_t j = i - n_vol;
+    int64_t per = (int64_t)n * n;
+    int face = (int)(j / per);
+    int64_t r = j % per;
+    int64_t u = r % n, v = r / n;
+    int axis = face / 2;
+    double val = (face & 1) ? 1.0 : 0.0;
+    int f0 = axis == 0 ? 1 : 0;
+    int f1 = axis == 2 ? 1 : 2;
+    double x[3];
+    x[axis] = val;
+    x[f0] = (u + 1) * h;
+    x[f1] = (v + 1) * h;
+    xyz[3 * i + 0] = x[0];
+    xyz[3 * i + 1] = x[1];
+    xyz[3 * i + 2] = x[2];
+  }
+}
+
+__device__ __forceinline__ int cell_coord(double x, int nl) {
+  int c = (int)floor(x * nl);
+  return c < 0 ? 0 : (c >= nl ? nl - 1 : c);
+}
+
+__global__ void k_leaf_keys_count(const double* xyz, int64_t n_vol, int64_t n_pts, int nl,
+                                  int* key, int* cnt_vol, int* cnt_bnd) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_pts) return;
+  int ix = cell_coord(xyz[3 * i], nl), iy = cell_coord(xyz[3 * i + 1], nl),
+      iz = cell_coord(xyz[3 * i + 2], nl);
+  int m = (int)morton_encode(ix, iy, iz);
+  key[i] = m;
+  atomicAdd(i < n_vol ? &cnt_vol[m] : &cnt_bnd[m], 1);
+}
+
+// exclusive scan of cnt_vol + cnt_bnd over nleaf entries; one block
+__global__ void k_scan_leaves(const int* cnt_vol, const int* cnt_bnd, int nleaf, int* leaf_start,
+                              int* leaf_mid, int* cursor_vol, int* cursor_bnd) {
+  __shared__ int partial[1024];
+  int tid = threadIdx.x;
+  int chunk = (nleaf + blockDim.x - 1) / blockDim.x;
+  int lo = tid * chunk, hi = min(nleaf, lo + chunk);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += cnt_vol[i] + cnt_bnd[i];
+  partial[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      int v = partial[i];
+      partial[i] = run;
+      run += v;
+    }
+    leaf_start[nleaf] = run;
+  }
+  __syncthreads();
+  int run = partial[tid];
+  for (int i = lo; i < hi; ++i) {
+    leaf_start[i] = run;
+    leaf_mid[i] = run + cnt_vol[i];
+    cursor_vol[i] = run;
+    cursor_bnd[i] = run + cnt_vol[i];
+    run += cnt_vol[i] + cnt_bnd[i];
+  }
+}
+
+__global__ void k_scatter(const int* key, int64_t n_vol, int64_t n_pts, int* cursor_vol,
+                          int* cursor_bnd, int64_t* orig) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_pts) return;
+  int m = key[i];
+  int pos = atomicAdd(i < n_vol ? &cursor_vol[m] : &cursor_bnd[m], 1);
+  orig[pos] = i;
+}
+
+// Order each leaf's volume and boundary segments by original id: the rank of
+// an element is the number of smaller ids in its segment.
+__global__ void k_sort_segments(const int* leaf_start, const int* leaf_mid, int64_t* orig,
+                                int64_t* tmp) {
+  int leaf = blockIdx.x;
+  for (int part = 0; part < 2; ++part) {
+    int lo = part == 0 ? leaf_start[leaf] : leaf_mid[leaf];
+    int hi = part == 0 ? leaf_mid[leaf] : leaf_start[leaf + 1];
+    int cnt = hi - lo;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      int64_t v = orig[lo + e];
+      int rank = 0;
+      for (int f = 0; f < cnt; ++f) rank += orig[lo + f] < v;
+      tmp[lo + rank] = v;
+    }
+  }
+}
+
+// sorted FP64 coordinates, FP32 coordinates relative to the point's leaf
+// centre (small numbers: differences inside the near field keep their
+// relative precision in FP32), and the inverse permutation
+__global__ void k_finalize_points(const int64_t* orig, const double* xyz_in, int64_t n_pts, int nl,
+                                  double* xyz, float* xyz32, int64_t* pos_of) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_pts) return;
+  int64_t o = orig[i];
+  double x = xyz_in[3 * o], y = xyz_in[3 * o + 1], z = xyz_in[3 * o + 2];
+  xyz[3 * i] = x;
+  xyz[3 * i + 1] = y;
+  xyz[3 * i + 2] = z;
+  double w = 1.0 / nl;
+  xyz32[4 * i] = (float)(x - (cell_coord(x, nl) + 0.5) * w);
+  xyz32[4 * i + 1] = (float)(y - (cell_coord(y, nl) + 0.5) * w);
+  xyz32[4 * i + 2] = (float)(z - (cell_coord(z, nl) + 0.5) * w);
+  xyz32[4 * i + 3] = 0.f;
+  pos_of[o] = i;
+}
+
+__global__ void k_leaf_flags(const int* cnt_vol, const int* cnt_bnd, int nleaf, int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nleaf) return;
+  flags[i] = (cnt_vol[i] > 0 ? 1 : 0) | (cnt_bnd[i] > 0 ? 2 : 0);
+}
+
+__global__ void k_parent_flags(const int* child_flags, int ncells, int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncells) return;
+  int f = 0;
+  for (int c = 0; c < 8; ++c) f |= child_flags[8 * i + c];
+  flags[i] = f;
+}
+
+// ---- lists
+
+__device__ __forceinline__ bool separated(int d2, int64_t num, int64_t den) {
+  return num * num * (int64_t)d2 > den * den;
+}
+__device__ __forceinline__ int floor_half(int x) { return x >= 0 ? x / 2 : -((1 - x) / 2); }
+__device__ __forceinline__ int pack_off(int dx, int dy, int dz) {
+  return (dx + 128) | ((dy + 128) << 8) | ((dz + 128) << 16);
+}
+
+__global__ void k_near_list(int64_t num, int64_t den, int R, int* out, int* count) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int c = 0;
+  for (int dz = -R; dz <= R; ++dz)
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx)
+        if (!separated(dx * dx + dy * dy + dz * dz, num, den)) out[c++] = pack_off(dx, dy, dz);
+  *count = c;
+}
+
+// one thread per parity class b = (bx, by, bz): offsets v in the box that are
+// separated and whose parents (at offset floor((b + v)/2)) are not
+__global__ void k_m2l_list(int64_t num, int64_t den, int box_r, int cap, int* off, int* box_index,
+                           int* count) {
+  int b = threadIdx.x;
+  if (b >= 8 || blockIdx.x != 0) return;
+  int bx = b & 1, by = (b >> 1) & 1, bz = (b >> 2) & 1;
+  int w = 2 * box_r + 1;
+  int c = 0;
+  for (int dz = -box_r; dz <= box_r; ++dz)
+    for (int dy = -box_r; dy <= box_r; ++dy)
+      for (int dx = -box_r; dx <= box_r; ++dx) {
+        if (!separated(dx * dx + dy * dy + dz * dz, num, den)) continue;
+        int px = floor_half(bx + dx), py = floor_half(by + dy), pz = floor_half(bz + dz);
+        if (separated(px * px + py * py + pz * pz, num, den)) continue;
+        if (c < cap) {
+          off[b * cap + c] = pack_off(dx, dy, dz);
+          box_index[b * cap + c] = (dx + box_r) + w * ((dy + box_r) + w * (dz + box_r));
+        }
+        ++c;
+      }
+  count[b] = c;
+}
+
+// Distinct M2L offsets over the eight classes get operator slots in box
+// order; the lists are repacked to stride `count[0]` and their box indices
+// replaced by slots.  One thread (tiny, one-time).
+__global__ void k_m2l_slots(int box, const int* count, int* off, int* box_index, int* slot,
+                            int* slot_off, int* nslots) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int cnt = count[0];
+  for (int i = 0; i < box; ++i) slot[i] = -1;
+  for (int b = 0; b < 8; ++b)
+    for (int i = 0; i < cnt; ++i) slot[box_index[b * box + i]] = 0;
+  int ns = 0;
+  for (int i = 0; i < box; ++i)
+    if (slot[i] == 0) slot[i] = ns++;
+  for (int b = 0; b < 8; ++b)
+    for (int i = 0; i < cnt; ++i) {
+      int o = off[b * box + i];
+      int sl = slot[box_index[b * box + i]];
+      slot_off[sl] = o;
+      off[b * cnt + i] = o;
+      box_index[b * cnt + i] = sl;
+    }
+  *nslots = ns;
+}
+
+// ---- self terms
+
+// radial integrals along a ray of length R from the singular point:
+//   Iv(a) = int_0^1 s e^{i a s} ds   (volume: s^2 ds times 1/(s R))
+//   Ip(a) = int_0^1 e^{i a s} ds     (panel:  s ds times 1/(s R))
+__device__ double2 radial_vol(double a) {
+  if (a < 1.0) {  // sum_m (i a)^m / (m! (m + 2))
+    double2 s = make_double2(0, 0), t = make_double2(1, 0);  // t = (ia)^m / m!
+    for (int m = 0; m < 40; ++m) {
+      s.x += t.x / (m + 2);
+      s.y += t.y / (m + 2);
+      double2 tn = make_double2(-t.y * a / (m + 1), t.x * a / (m + 1));
+      t = tn;
+    }
+    return s;
+  }
+  double sa, ca;
+  sincos(a, &sa, &ca);
+  // e^{ia}/(ia) + (e^{ia} - 1)/a^2
+  return make_double2(sa / a + (ca - 1.0) / (a * a), -ca / a + sa / (a * a));
+}
+__device__ double2 radial_panel(double a) {
+  if (a < 1.0) {  // sum_m (i a)^m / (m + 1)!
+    double2 s = make_double2(0, 0), t = make_double2(1, 0);  // (ia)^m / (m+1)!
+    for (int m = 0; m < 40; ++m) {
+      s.x += t.x;
+      s.y += t.y;
+      double2 tn = make_double2(-t.y * a / (m + 2), t.x * a / (m + 2));
+      t = tn;
+    }
+    return s;
+  }
+  double sa, ca;
+  sincos(a, &sa, &ca);
+  // (e^{ia} - 1)/(ia)
+  return make_double2(sa / a, (1.0 - ca) / a);
+}
+
+// s_vol = 6 (h/2) int_{face} Iv(k R) / (4 pi R) dA,  R = |(h/2, u, v)|
+// s_bnd = 4 (h/2) int_{edge} Ip(k R) / (4 pi R) du,  R = |(h/2, u)|
+// (pyramids / triangles with apex at the singular point, radial part exact)
+__global__ void k_self_terms(double h, double k, double2* out) {
+  constexpr int NQ = 32;
+  __shared__ double xg[NQ], wg[NQ];
+  __shared__ double2 red[256];
+  if (threadIdx.x == 0) gauss_legendre(NQ, xg, wg);
+  __syncthreads();
+  const double hh = 0.5 * h;
+  const double inv4pi = 0.25 / M_PI;
+  double2 acc = make_double2(0, 0);
+  for (int q = threadIdx.x; q < NQ * NQ; q += blockDim.x) {
+    int i = q % NQ, j = q / NQ;
+    double u = hh * xg[i], v = hh * xg[j];
+    double R = sqrt(hh * hh + u * u + v * v);
+    double2 I = radial_vol(k * R);
+    double wt = hh * wg[i] * hh * wg[j] * inv4pi / R;
+    acc.x += wt * I.x;
+    acc.y += wt * I.y;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[threadIdx.x].x += red[threadIdx.x + s].x;
+      red[threadIdx.x].y += red[threadIdx.x + s].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = make_double2(6 * hh * red[0].x, 6 * hh * red[0].y);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 a2 = make_double2(0, 0);
+    for (int i = 0; i < NQ; ++i) {
+      double u = hh * xg[i];
+      double R = sqrt(hh * hh + u * u);
+      double2 I = radial_panel(k * R);
+      double wt = hh * wg[i] * inv4pi / R;
+      a2.x += wt * I.x;
+      a2.y += wt * I.y;
+    }
+    out[1] = make_double2(4 * hh * a2.x, 4 * hh * a2.y);
+  }
+}
+
+}  // namespace
+
+int build_geometry_and_sort(fmm_tree* t, const double* d_vol, const double* d_bnd, cudaStream_t s) {
+  const int64_t N = t->n_pts;
+  const int nleaf = 1 << (3 * t->L);
+  double* xyz_in = nullptr;
+  int *key = nullptr, *cnt_vol = nullptr, *cnt_bnd = nullptr, *cur_vol = nullptr, *cur_bnd = nullptr;
+  int64_t* tmp = nullptr;
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&xyz_in, sizeof(double) * 3 * std::max<int64_t>(N, 1), s));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&key, sizeof(int) * std::max<int64_t>(N, 1), s));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&cnt_vol, sizeof(int) * nleaf * 4, s));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&tmp, sizeof(int64_t) * std::max<int64_t>(N, 1), s));
+  cnt_bnd = cnt_vol + nleaf;
+  cur_vol = cnt_vol + 2 * nleaf;
+  cur_bnd = cnt_vol + 3 * nleaf;
+  HFMM_CUDA_TRY(cudaMemsetAsync(cnt_vol, 0, sizeof(int) * nleaf * 2, s));
+
+  if (t->lattice) {
+    k_lattice_points<<<ceil_div(N, 256), 256, 0, s>>>(t->n, t->h, t->n_vol, t->n_bnd, xyz_in);
+  } else {
+    if (t->n_vol) HFMM_CUDA_TRY(cudaMemcpyAsync(xyz_in, d_vol, sizeof(double) * 3 * t->n_vol,
+                                                cudaMemcpyDeviceToDevice, s));
+    if (t->n_bnd) HFMM_CUDA_TRY(cudaMemcpyAsync(xyz_in + 3 * t->n_vol, d_bnd,
+                                                sizeof(double) * 3 * t->n_bnd,
+                                                cudaMemcpyDeviceToDevice, s));
+  }
+  k_leaf_keys_count<<<ceil_div(N, 256), 256, 0, s>>>(xyz_in, t->n_vol, N, t->nlv, key, cnt_vol,
+                                                     cnt_bnd);
+  k_scan_leaves<<<1, 1024, 0, s>>>(cnt_vol, cnt_bnd, nleaf, t->leaf_start, t->leaf_mid, cur_vol,
+                                   cur_bnd);
+  k_scatter<<<ceil_div(N, 256), 256, 0, s>>>(key, t->n_vol, N, cur_vol, cur_bnd, t->orig);
+  k_sort_segments<<<nleaf, 128, 0, s>>>(t->leaf_start, t->leaf_mid, t->orig, tmp);
+  HFMM_CUDA_TRY(cudaMemcpyAsync(t->orig, tmp, sizeof(int64_t) * N, cudaMemcpyDeviceToDevice, s));
+  k_finalize_points<<<ceil_div(N, 256), 256, 0, s>>>(t->orig, xyz_in, N, t->nlv, t->xyz,
+                                                     t->xyz32, t->pos_of);
+  // occupancy flags, leaf level then upwards
+  k_leaf_flags<<<ceil_div(nleaf, 256), 256, 0, s>>>(cnt_vol, cnt_bnd, nleaf,
+                                                    t->flags + t->level_off[t->L]);
+  for (int l = t->L - 1; l >= 0; --l) {
+    int nc = 1 << (3 * l);
+    k_parent_flags<<<ceil_div(nc, 256), 256, 0, s>>>(t->flags + t->level_off[l + 1], nc,
+                                                     t->flags + t->level_off[l]);
+  }
+  HFMM_TRY(hfmm_last_launch());
+  // near-field pair count (statistics)
+  std::vector<int> hv(nleaf), hb(nleaf);
+  HFMM_CUDA_TRY(cudaMemcpyAsync(hv.data(), cnt_vol, sizeof(int) * nleaf, cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaMemcpyAsync(hb.data(), cnt_bnd, sizeof(int) * nleaf, cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  t->p2p_pairs = 0;
+  {
+    const int R = (int)(t->th_den / t->th_num) + 1;
+    for (int m = 0; m < nleaf; ++m) {
+      int64_t cm = hv[m] + hb[m];
+      if (!cm) continue;
+      int ix, iy, iz;
+      morton_decode((uint64_t)m, ix, iy, iz);
+      for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+          for (int dx = -R; dx <= R; ++dx) {
+            int64_t d2 = dx * dx + dy * dy + dz * dz;
+            if (t->th_num * t->th_num * d2 > t->th_den * t->th_den) continue;
+            int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+            if (jx < 0 || jy < 0 || jz < 0 || jx >= t->nlv || jy >= t->nlv || jz >= t->nlv) continue;
+            int o = (int)morton_encode(jx, jy, jz);
+            t->p2p_pairs += cm * (hv[o] + hb[o]);
+          }
+    }
+    t->p2p_pairs -= N;  // j != i
+  }
+  cudaFreeAsync(xyz_in, s);
+  cudaFreeAsync(key, s);
+  cudaFreeAsync(cnt_vol, s);
+  cudaFreeAsync(tmp, s);
+  return hfmm_last_launch();
+}
+
+int build_lists(fmm_tree* t, cudaStream_t s) {
+  const int Rn = (int)(t->th_den / t->th_num);  // floor(1/theta): near offsets lie in [-Rn, Rn]
+  t->box_r = 2 * Rn + 1;                         // M2L offsets: 2u + c - b with |u| <= Rn
+  const int w = 2 * t->box_r + 1;
+  const int box = w * w * w;
+  int* d_count = nullptr;
+  int* d_slot = nullptr;
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&d_count, sizeof(int) * 16, s));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&d_slot, sizeof(int) * box, s));
+  const int near_cap = (2 * Rn + 3) * (2 * Rn + 3) * (2 * Rn + 3);
+  HFMM_TRY(tree_alloc_t(t, &t->near_off, near_cap));
+  k_near_list<<<1, 1, 0, s>>>(t->th_num, t->th_den, Rn + 1, t->near_off, d_count);
+  HFMM_TRY(tree_alloc_t(t, &t->m2l_off, 8 * box));
+  HFMM_TRY(tree_alloc_t(t, &t->m2l_box_index, 8 * box));
+  HFMM_TRY(tree_alloc_t(t, &t->m2l_slot_off, box));
+  k_m2l_list<<<1, 32, 0, s>>>(t->th_num, t->th_den, t->box_r, box, t->m2l_off, t->m2l_box_index,
+                              d_count + 1);
+  k_m2l_slots<<<1, 1, 0, s>>>(box, d_count + 1, t->m2l_off, t->m2l_box_index, d_slot,
+                              t->m2l_slot_off, d_count + 9);
+  HFMM_TRY(hfmm_last_launch());
+  int hc[10];
+  HFMM_CUDA_TRY(cudaMemcpyAsync(hc, d_count, sizeof(int) * 10, cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFreeAsync(d_count, s);
+  cudaFreeAsync(d_slot, s);
+  t->near_count = hc[0];
+  for (int b = 1; b < 8; ++b)
+    if (hc[1 + b] != hc[1]) return HFMM_ERR_UNSUPPORTED;
+  t->m2l_count = hc[1];
+  t->box_cells = hc[9];  // number of distinct M2L offsets = operator slots per level
+  // statistics: far-field cell pairs over all levels, every cell a target
+  std::vector<int> off(8 * (size_t)box);
+  HFMM_CUDA_TRY(cudaMemcpy(off.data(), t->m2l_off, sizeof(int) * off.size(), cudaMemcpyDeviceToHost));
+  t->m2l_pairs = 0;
+  for (int l = 2; l <= t->L; ++l) {
+    int sl = 1 << l;
+    for (int b = 0; b < 8; ++b) {
+      int bb[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+      for (int i = 0; i < t->m2l_count; ++i) {
+        int o = off[(size_t)b * t->m2l_count + i];
+        int d[3] = {(o & 255) - 128, ((o >> 8) & 255) - 128, ((o >> 16) & 255) - 128};
+        int64_t cnt = 1;
+        for (int ax = 0; ax < 3; ++ax) {
+          int64_t c = 0;
+          for (int x = bb[ax]; x < sl; x += 2)
+            if (x + d[ax] >= 0 && x + d[ax] < sl) ++c;
+          cnt *= c;
+        }
+        t->m2l_pairs += cnt;
+      }
+    }
+  }
+  return HFMM_OK;
+}
+
+int build_self_terms(fmm_tree* t, cudaStream_t s) {
+  if (!t->lattice) {
+    t->s_vol = t->s_bnd = t->sigma_vol = t->sigma_bnd = make_double2(0, 0);
+    return HFMM_OK;
+  }
+  double2* d = nullptr;
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&d, sizeof(double2) * 2, s));
+  k_self_terms<<<1, 256, 0, s>>>(t->h, t->k, d);
+  HFMM_TRY(hfmm_last_launch());
+  double2 hs[2];
+  HFMM_CUDA_TRY(cudaMemcpyAsync(hs, d, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFreeAsync(d, s);
+  t->s_vol = hs[0];
+  t->s_bnd = hs[1];
+  const double h3 = t->h * t->h * t->h, h2 = t->h * t->h;
+  t->sigma_vol = make_double2(hs[0].x / h3, hs[0].y / h3);
+  t->sigma_bnd = make_double2(hs[1].x / h2, hs[1].y / h2);
+  return HFMM_OK;
+}

@@ -1,0 +1,108 @@
+// Internal state of an fmm_tree handle and the entry points shared between
+// the translation units of the library.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+// One device allocation tracked by the handle.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct fmm_tree_ext;  // solver workspaces (capi.cu)
+
+struct fmm_tree {
+  fmm_tree_ext* ext = nullptr;
+  // ---- problem
+  int n = 0;             // interior nodes per axis (lattice trees)
+  int lattice = 1;       // 1: points are the n^3 nodes and 6 n^2 panels
+  int64_t n_vol = 0, n_bnd = 0, n_pts = 0;
+  double h = 0.0, k = 0.0;
+  int p = 0, P = 0;      // order and coefficients per expansion (p^2)
+  int precision = HFMM_FP64;
+  int leaf_size = 0;
+  double theta = 0.0;
+  int64_t th_num = 0, th_den = 1;  // theta as a rational number
+  int L = 0;             // leaf level
+  int nlv = 0;           // lattice leaf cells per axis = 2^L
+
+  // ---- points in sorted (leaf-Morton) order: within a leaf volume points
+  //      first, then boundary points, each by original index
+  double* xyz = nullptr;        // [n_pts][3] sorted coordinates (FP64)
+  float* xyz32 = nullptr;       // [n_pts][4] sorted coordinates (FP32, w unused)
+  int64_t* orig = nullptr;      // sorted position -> original id (vol ids, then n_vol + bnd id)
+  int64_t* pos_of = nullptr;    // original id -> sorted position
+  int* leaf_start = nullptr;    // [8^L + 1] first sorted position of each leaf
+  int* leaf_mid = nullptr;      // [8^L] first boundary point of each leaf
+  int* flags = nullptr;         // per level, per Morton cell: bit0 volume points, bit1 boundary
+  int64_t level_off[HFMM_MAX_LEVEL + 2] = {0};  // first cell of level l in the per-cell arrays
+  int64_t total_cells = 0;
+
+  // ---- interaction lists (offsets in cell units)
+  int near_count = 0;
+  int* near_off = nullptr;      // [near_count] packed offsets (dx,dy,dz) each in 8 bits + 128
+  int box_r = 0;                // M2L offsets lie in [-box_r, box_r]^3
+  int m2l_count = 0;            // offsets per parity class (same for all classes)
+  int* m2l_off = nullptr;       // [8][m2l_count] packed offsets
+  int* m2l_box_index = nullptr; // [8][m2l_count] operator slot of each list entry
+  int* m2l_slot_off = nullptr;  // [slots] packed offset of each operator slot
+
+  // ---- operators (FP64 master copy; FP32 copy for the FP32 form)
+  double2* op_m2m = nullptr;    // [L+1][8][P][P]   row a' (out), column a (in)
+  double2* op_l2l = nullptr;    // [L+1][8][P][P]
+  double2* op_m2l = nullptr;    // [L+1][box^3][P][P]
+  float2* op_m2m32 = nullptr;
+  float2* op_l2l32 = nullptr;
+  float2* op_m2l32 = nullptr;
+  int64_t box_cells = 0;        // distinct M2L offsets = operator slots per level
+
+  // ---- singular self coefficients per unit weight
+  double2 sigma_vol = {0, 0};   // s_Omega / h^3
+  double2 sigma_bnd = {0, 0};   // s_Gamma / h^2
+  double2 s_vol = {0, 0}, s_bnd = {0, 0};
+
+  // ---- expansions and sorted work vectors (precision T)
+  void* M = nullptr;            // [total_cells][P]
+  void* Lc = nullptr;           // [total_cells][P]
+  void* qs = nullptr;           // [n_pts] sorted weights
+  void* phis = nullptr;         // [n_pts] sorted potentials
+
+  // ---- preconditioner work (complex128)
+  double2* g_bnd = nullptr;     // [n_bnd]
+  double2* q_bnd = nullptr;     // [n_bnd]
+
+  // ---- counters
+  int64_t m2l_pairs = 0, p2p_pairs = 0;
+  double ms_last_apply = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  std::vector<DevBuf> bufs;
+  int64_t device_bytes = 0;
+};
+
+// allocation helper owned by the handle
+int tree_alloc(fmm_tree* t, void** ptr, size_t bytes);
+template <typename X>
+inline int tree_alloc_t(fmm_tree* t, X** ptr, size_t count) {
+  return tree_alloc(t, (void**)ptr, count * sizeof(X));
+}
+
+// tree.cu
+int build_geometry_and_sort(fmm_tree* t, const double* d_vol, const double* d_bnd, cudaStream_t s);
+int build_lists(fmm_tree* t, cudaStream_t s);
+int build_self_terms(fmm_tree* t, cudaStream_t s);
+
+// operators.cu
+int build_operators(fmm_tree* t, cudaStream_t s);
+
+// fmm.cu: sorted-weight gather, FMM core over the sorted vectors, scatter
+int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol,
+               const double2* q_bnd, double scale_bnd, cudaStream_t s);
+int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
+int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cudaStream_t s);
+
+// krylov.cu
+int fdm_apply_dev(int n, double h, double k, const double2* u, double2* out, cudaStream_t s);

@@ -1,0 +1,232 @@
+"""Thin ctypes binding of the C ABI in include/hfmm.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library libhfmm.so.  PyTorch supplies device memory (complex128 tensors on a
+CUDA device) and the current stream.  If the library is missing this module
+raises on first use; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HFMM_OK = 0
+HFMM_ERR_INVALID_ARG = -1
+HFMM_ERR_CUDA = -2
+HFMM_ERR_NOMEM = -3
+HFMM_ERR_NONFINITE = -4
+HFMM_ERR_NOT_CONVERGED = -5
+HFMM_ERR_TIMEOUT = -6
+HFMM_ERR_UNSUPPORTED = -7
+
+HFMM_FP64 = 0
+HFMM_FP32 = 1
+SET_VOL = 1
+SET_BND = 2
+FWD = 0
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhfmm.so")
+
+
+class hfmm_params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("theta", ctypes.c_double), ("leaf_size", ctypes.c_int),
+                ("k", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class hfmm_gmres_params(ctypes.Structure):
+    _fields_ = [("restart_m", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("inner_maxit", ctypes.c_int),
+                ("inner_m", ctypes.c_int)]
+
+
+class hfmm_gmres_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("inner_iters_total", ctypes.c_int), ("status", ctypes.c_int),
+                ("relres_est", ctypes.c_double), ("relres_true", ctypes.c_double),
+                ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int)]
+
+
+class hfmm_stats(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("p", ctypes.c_int), ("n_vol", ctypes.c_int64),
+                ("n_bnd", ctypes.c_int64), ("leaves", ctypes.c_int64),
+                ("m2l_pairs", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("ms_last_apply", ctypes.c_double)]
+
+
+# name -> (restype, argtypes) for every entry point of include/hfmm.h
+SIGNATURES = {
+    "hfmm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fmm_build_tree": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.POINTER(hfmm_params), ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "fmm_destroy_tree": (None, [ctypes.c_void_p]),
+    "fmm_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                 ctypes.c_void_p]),
+    "fmm_precond_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "hfmm_fdm_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "gmres_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(hfmm_gmres_params),
+                                   ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
+    "fmm_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hfmm_stats)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libhfmm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run python -m paper_1608_02461_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class HfmmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {lib().hfmm_error_string(status).decode()} ({status})")
+
+
+def _check(status: int, what: str):
+    if status != HFMM_OK:
+        raise HfmmError(status, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_c128(t, n, name):
+    torch = _torch()
+    if t.dtype != torch.complex128 or not t.is_cuda or t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA complex128 tensor with {n} entries")
+    return t
+
+
+@dataclass
+class GmresInfo:
+    iters: int
+    restarts: int
+    inner_iters_total: int
+    status: int
+    relres_est: float
+    relres_true: float
+    history: list
+
+
+class Tree:
+    """Handle of fmm_build_tree: octree, lists, operators and self terms for
+    one grid (n), wavenumber k and expansion order p."""
+
+    def __init__(self, n: int, k: float, p: int, theta: float = 0.4, leaf: int = 64,
+                 precision: str = "fp64", vol_xyz=None, bnd_xyz=None, stream=None):
+        L = lib()
+        self.n, self.k, self.p, self.theta, self.leaf = n, k, p, theta, leaf
+        self.precision = precision
+        prm = hfmm_params(p, theta, leaf, k, HFMM_FP32 if precision == "fp32" else HFMM_FP64)
+        handle = ctypes.c_void_p()
+        n_vol = vol_xyz.shape[0] if vol_xyz is not None else n ** 3
+        n_bnd = bnd_xyz.shape[0] if bnd_xyz is not None else 6 * n * n
+        self._keep = (vol_xyz, bnd_xyz)
+        st = L.fmm_build_tree(n, _ptr(vol_xyz), n_vol, _ptr(bnd_xyz), n_bnd, ctypes.byref(prm),
+                              _stream_ptr(stream), ctypes.byref(handle))
+        _check(st, "fmm_build_tree")
+        self._h = handle
+        self.n_vol, self.n_bnd = n_vol, n_bnd
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fmm_destroy_tree(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, q_vol=None, q_bnd=None, src=SET_VOL | SET_BND, tgt=SET_VOL | SET_BND,
+              phi_vol=None, phi_bnd=None, stream=None):
+        torch = _torch()
+        dev = (q_vol if q_vol is not None else q_bnd).device
+        if (tgt & SET_VOL) and phi_vol is None:
+            phi_vol = torch.empty(self.n_vol, dtype=torch.complex128, device=dev)
+        if (tgt & SET_BND) and phi_bnd is None:
+            phi_bnd = torch.empty(self.n_bnd, dtype=torch.complex128, device=dev)
+        if q_vol is not None:
+            _dev_c128(q_vol, self.n_vol, "q_vol")
+        if q_bnd is not None:
+            _dev_c128(q_bnd, self.n_bnd, "q_bnd")
+        st = lib().fmm_apply(self._h, src, tgt, _ptr(q_vol), _ptr(q_bnd), _ptr(phi_vol),
+                             _ptr(phi_bnd), FWD, _stream_ptr(stream))
+        _check(st, "fmm_apply")
+        return phi_vol, phi_bnd
+
+    def precond(self, r, z=None, inner_rtol=1e-4, inner_maxit=200, inner_m=50, stream=None):
+        torch = _torch()
+        _dev_c128(r, self.n_vol, "r")
+        if z is None:
+            z = torch.empty_like(r)
+        its = ctypes.c_int(0)
+        st = lib().fmm_precond_apply(self._h, _ptr(r), _ptr(z), inner_rtol, inner_maxit, inner_m,
+                                     ctypes.byref(its), _stream_ptr(stream))
+        _check(st, "fmm_precond_apply")
+        return z, its.value
+
+    def fdm(self, u, out=None, stream=None):
+        torch = _torch()
+        _dev_c128(u, self.n_vol, "u")
+        if out is None:
+            out = torch.empty_like(u)
+        _check(lib().hfmm_fdm_apply(self._h, _ptr(u), _ptr(out), _stream_ptr(stream)),
+               "hfmm_fdm_apply")
+        return out
+
+    def gmres(self, b, x=None, restart=30, rtol=1e-6, maxit=0, inner_rtol=1e-4, inner_maxit=200,
+              inner_m=50, history_len=2000, raise_on_nonconvergence=False, stream=None):
+        torch = _torch()
+        _dev_c128(b, self.n_vol, "b")
+        if x is None:
+            x = torch.zeros_like(b)
+        gp = hfmm_gmres_params(restart, rtol, maxit, inner_rtol, inner_maxit, inner_m)
+        hist = (ctypes.c_double * history_len)()
+        info = hfmm_gmres_info(0, 0, 0, 0, 0.0, 0.0, hist, history_len)
+        st = lib().gmres_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(gp), ctypes.byref(info),
+                               _stream_ptr(stream))
+        if st != HFMM_OK and (st != HFMM_ERR_NOT_CONVERGED or raise_on_nonconvergence):
+            raise HfmmError(st, "gmres_solve")
+        gi = GmresInfo(info.iters, info.restarts, info.inner_iters_total, info.status,
+                       info.relres_est, info.relres_true, list(hist[:min(info.iters, history_len)]))
+        return x, gi
+
+    def stats(self) -> hfmm_stats:
+        s = hfmm_stats()
+        _check(lib().fmm_get_stats(self._h, ctypes.byref(s)), "fmm_get_stats")
+        return s

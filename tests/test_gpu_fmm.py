@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA FMM stages, preconditioner, FDM operator and GMRES
+against the independent FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 FMM 1e-11 relative L2 (both sides compute the same truncated
+expansion; only rounding differs).  FP32 form: errors are reported and bounded
+by the FP32 arithmetic of the P2P/M2L sums (5e-5 relative L2).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bem, fdm, fmm as ofmm, gmres as ogmres  # noqa: E402
+from paper_1608_02461_gb300 import hfmm, inputs  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def run_apply(tree, qv, qb, src, tgt):
+    tv = torch.from_numpy(qv).to(DEV) if qv is not None else None
+    tb = torch.from_numpy(qb).to(DEV) if qb is not None else None
+    pv, pb = tree.apply(tv, tb, src=src, tgt=tgt)
+    torch.cuda.synchronize()
+    out = []
+    if tgt & hfmm.SET_VOL:
+        out.append(pv.cpu().numpy())
+    if tgt & hfmm.SET_BND:
+        out.append(pb.cpu().numpy())
+    return np.concatenate(out)
+
+
+def oracle_apply(pr, qv, qb, src, tgt):
+    q = np.concatenate([qv if qv is not None else np.zeros(pr.NO, complex),
+                        qb if qb is not None else np.zeros(pr.NG, complex)])
+    sm = np.zeros(pr.NO + pr.NG, bool)
+    tm = np.zeros(pr.NO + pr.NG, bool)
+    if src & 1:
+        sm[:pr.NO] = True
+    if src & 2:
+        sm[pr.NO:] = True
+    if tgt & 1:
+        tm[:pr.NO] = True
+    if tgt & 2:
+        tm[pr.NO:] = True
+    phi = pr.fmm.apply(q, sm, tm, pr.sigma)
+    return phi[tm]
+
+
+CASES = [
+    # n, k, p, leaf, theta  -- L = 3 with a ragged lattice-to-leaf map
+    (16, 4.0, 4, 32, 0.4),
+    (13, 9.0, 6, 16, 0.35),
+    (10, 2.5, 5, 8, 0.4),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_fmm_apply_fp64_matches_oracle(case):
+    n, k, p, leaf, theta = case
+    tree = hfmm.Tree(n, k, p, theta, leaf, "fp64")
+    pr = bem.Problem(n, k, p, leaf, theta)
+    assert tree.stats().L == pr.fmm.L
+    qv = inputs.complex_normal(n ** 3, 100 + n)
+    qb = inputs.complex_normal(6 * n * n, 200 + n)
+    for src, tgt in [(3, 3), (1, 2), (2, 2), (3, 1), (1, 1)]:
+        got = run_apply(tree, qv if src & 1 else None, qb if src & 2 else None, src, tgt)
+        ref = oracle_apply(pr, qv if src & 1 else None, qb if src & 2 else None, src, tgt)
+        assert rel(got, ref) < 1e-11, (case, src, tgt, rel(got, ref))
+    tree.close()
+
+
+def test_fmm_apply_fp32_error_bounded():
+    n, k, p, leaf, theta = 16, 4.0, 4, 32, 0.4
+    tree = hfmm.Tree(n, k, p, theta, leaf, "fp32")
+    pr = bem.Problem(n, k, p, leaf, theta)
+    qv = inputs.complex_normal(n ** 3, 7)
+    qb = inputs.complex_normal(6 * n * n, 8)
+    got = run_apply(tree, qv, qb, 3, 3)
+    ref = oracle_apply(pr, qv, qb, 3, 3)
+    err = rel(got, ref)
+    print(f"fp32 rel err vs fp64 oracle: {err:.3e}")
+    assert err < 5e-5
+
+
+def test_fmm_high_order_matches_direct_sum():
+    n, k = 9, 5.0
+    tree = hfmm.Tree(n, k, 14, 0.4, 8, "fp64")
+    pr = bem.Problem(n, k, 4, 8, 0.4)
+    qv = inputs.complex_normal(n ** 3, 31)
+    qb = inputs.complex_normal(6 * n * n, 32)
+    got = run_apply(tree, qv, qb, 3, 3)
+    q = np.concatenate([qv, qb])
+    allm = np.ones(len(q), bool)
+    ref = ofmm.direct_sum(pr.points, q, allm, allm, k, pr.sigma)
+    assert rel(got, ref) < 3e-9   # truncation error of p = 14 at theta = 0.4
+
+
+def test_fdm_matches_oracle():
+    n, k = 12, 6.0
+    tree = hfmm.Tree(n, k, 4, 0.4, 32, "fp64")
+    u = inputs.complex_normal(n ** 3, 5)
+    out = tree.fdm(torch.from_numpy(u).to(DEV)).cpu().numpy()
+    ref = fdm.fdm_apply(u, n, k)
+    assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_precond_matches_oracle():
+    n, k, p, leaf, theta = 10, 4.0, 5, 8, 0.4
+    tree = hfmm.Tree(n, k, p, theta, leaf, "fp64")
+    pr = bem.Problem(n, k, p, leaf, theta)
+    r = inputs.complex_normal(n ** 3, 41)
+    z, its = tree.precond(torch.from_numpy(r).to(DEV), inner_rtol=1e-13, inner_maxit=300, inner_m=300)
+    zr, its_ref = pr.precond(r, inner_rtol=1e-13, inner_maxit=300, inner_m=300)
+    # both inner solves stop at 1e-13 relative residual; the boundary operator's
+    # conditioning amplifies that difference (bounded here by 1e-10)
+    assert rel(z.cpu().numpy(), zr) < 1e-10
+    assert abs(its - its_ref) <= 1
+
+
+def test_gmres_iterations_match_oracle():
+    w = inputs.WORKLOADS["helmholtz_n16_k4_p4"]
+    n, k = w["n"], w["k"]
+    tree = hfmm.Tree(n, k, w["p"], w["theta"], w["leaf"], "fp64")
+    b = inputs.workload_rhs("helmholtz_n16_k4_p4")
+    x, info = tree.gmres(torch.from_numpy(b).to(DEV), restart=w["restart"], rtol=1e-6,
+                         inner_rtol=1e-4)
+    xs = x.cpu().numpy()
+    res = np.linalg.norm(b - fdm.fdm_apply(xs, n, k)) / np.linalg.norm(b)
+    assert info.status == 0 and res < 1e-6
+    assert abs(info.relres_true - res) < 1e-9
+    pr = bem.Problem(n, k, w["p"], w["leaf"], w["theta"])
+    _, oi = ogmres.fgmres(lambda u: fdm.fdm_apply(u, n, k), b,
+                          lambda r: pr.precond(r, inner_rtol=1e-4)[0], m=w["restart"], rtol=1e-6)
+    assert abs(info.iters - oi["iters"]) <= 1, (info.iters, oi["iters"])
+
+
+def test_gmres_fp32_form_converges():
+    w = inputs.WORKLOADS["helmholtz_n16_k4_p4"]
+    n, k = w["n"], w["k"]
+    t64 = hfmm.Tree(n, k, w["p"], w["theta"], w["leaf"], "fp64")
+    t32 = hfmm.Tree(n, k, w["p"], w["theta"], w["leaf"], "fp32")
+    b = torch.from_numpy(inputs.workload_rhs("helmholtz_n16_k4_p4")).to(DEV)
+    _, i64 = t64.gmres(b, restart=30, rtol=1e-6, inner_rtol=1e-4)
+    x, i32 = t32.gmres(b, restart=30, rtol=1e-6, inner_rtol=1e-4)
+    assert i32.status == 0 and i32.relres_true < 1e-6
+    assert i32.iters <= int(np.ceil(1.1 * i64.iters)) + 1
+
+
+def test_gmres_not_converged_status():
+    n, k = 8, 4.0
+    tree = hfmm.Tree(n, k, 4, 0.4, 8, "fp64")
+    b = torch.from_numpy(inputs.rhs("uniform_real", n, 3)).to(DEV)
+    x, info = tree.gmres(b, restart=2, rtol=1e-14, maxit=3, inner_rtol=1e-3)
+    assert info.status == hfmm.HFMM_ERR_NOT_CONVERGED and info.iters == 3
+    with pytest.raises(hfmm.HfmmError):
+        tree.gmres(b, restart=2, rtol=1e-14, maxit=3, raise_on_nonconvergence=True)
+
+
+def test_build_is_deterministic():
+    n, k = 12, 7.0
+    q = torch.from_numpy(inputs.complex_normal(n ** 3, 9)).to(DEV)
+    outs = []
+    for _ in range(2):
+        t = hfmm.Tree(n, k, 5, 0.4, 16, "fp64")
+        pv, _ = t.apply(q, None, src=1, tgt=1)
+        outs.append(pv.cpu().numpy())
+        t.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_explicit_points_direct_sum():
+    """Caller-supplied points (no lattice, no self terms): the FMM converges to
+    the plain N-body sum of Sec. 5.1."""
+    N = 700
+    pts = inputs.uniform_points(N, 3)
+    q = inputs.complex_normal(N, 4)
+    k = 6.0
+    t = hfmm.Tree(0, k, 12, 0.4, 8, "fp64", vol_xyz=torch.from_numpy(pts).to(DEV))
+    pv, _ = t.apply(torch.from_numpy(q).to(DEV), None, src=1, tgt=1)
+    got = pv.cpu().numpy()
+    allm = np.ones(N, bool)
+    ref = ofmm.direct_sum(pts, q, allm, allm, k, np.zeros(N))
+    assert rel(got, ref) < 1e-7
+    # the oracle's FMM on the same points agrees to rounding
+    o = ofmm.FMM(pts, N, 8, 0.4, k, 12).apply(q, allm, allm, np.zeros(N))
+    assert rel(got, o) < 1e-11
