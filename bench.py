@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Benchmark of the FMM-preconditioned 3D Helmholtz solve on GB300.
+
+One step = one right-preconditioned GMRES solve to a relative residual of
+1e-6 of the 7-point FDM system -Lap u - k^2 u = f on 64^3 interior nodes
+(k = 16, p = 6, leaf 64, theta = 0.4, GMRES(50), f = 8 Gaussian sources on a
+uniform[-1,1] background), preconditioned by the BEM-coupled FMM with its FMM
+stages in FP32 (complex64) and all Krylov arithmetic in FP64.  The tree and
+operators are built before the timed region (reported as build_s).
+
+Printed JSON line (rank 0):
+  value        seconds per solve (time-to-1e-6, device time, inputs resident)
+  e2e          the same through host buffers (H2D of f, D2H of u inside)
+  roofline     dominant stage from live CUDA-event stage timers
+  cpu_baseline the FP64 CPU oracle on a bounded sample, scaled to one solve
+  fp64         the plain FP64 form of the same solve (time, iterations)
+  fmm_apply_mpts_s  (N_vol + N_bnd) / time of one full FMM apply (FP32 form)
+
+--impl reference times the oracle alone on the host (bounded sample).
+Multi-GPU (torchrun): every rank solves its own replica (replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GMRES time-to-1e-6 and FMM apply Mpts/s: FP32/batched vs plain FP64, same GB300"
+WORKLOAD = "helmholtz_n64_k16_p6"
+
+# GB300: 152 SMs, 128 FP32 lanes per SM, 2 flop per FMA, 2070 MHz maximum SM clock
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (vendor figure)
+P2P_FLOP_PER_PAIR = 23      # 3 sub, 5 r^2, rsqrt, 1/r, kr, sin, cos, 2 scale, 8 complex MAC
+L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, enabled, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu_index = gpu_index
+        if not enabled:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier_max(value, world, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle timing
+
+def oracle_sample(w, inner_per_apply, outer_iters, leaf_fraction=1.0 / 16):
+    """Time the FP64 CPU oracle on a bounded sample of one solve and scale it to
+    seconds per solve.  The far field (P2M, M2M, M2L, L2L) of the three FMM
+    passes of a preconditioner application runs in full; the near field (P2P)
+    runs for the targets in a random subset of leaves and is scaled by the
+    fraction of target points sampled.  Returns (seconds_per_solve, text)."""
+    from oracle import bem, fdm
+    t0 = time.perf_counter()
+    pr = bem.Problem(w["n"], w["k"], w["p"], w["leaf"], w["theta"])
+    f = pr.fmm
+    rng = np.random.default_rng(0)
+    q = rng.standard_normal(pr.NO + pr.NG) + 1j * rng.standard_normal(pr.NO + pr.NG)
+
+    def far(src, tgt):
+        L = f.L
+        M = {L: f.p2m(q, src)}
+        for l in range(L - 1, 1, -1):
+            M[l] = f.m2m(M[l + 1], l)
+        Lc = {l: f.m2l(M[l], l) for l in range(2, L + 1)}
+        for l in range(2, L):
+            Lc[l + 1] = f.l2l(Lc[l], Lc[l + 1], l)
+        return f.l2p(Lc[L], tgt)
+
+    def timed(fn):
+        a = time.perf_counter()
+        fn()
+        return time.perf_counter() - a
+
+    far(pr.vol, pr.bnd)          # translation operators are built on first use: not timed
+    leaves = np.unique(f.tree.leaf)
+    pick = rng.choice(leaves, size=max(1, int(leaf_fraction * len(leaves))), replace=False)
+    sel = np.isin(f.tree.leaf, pick)
+    tv = pr.vol & sel
+    tb = pr.bnd & sel
+    sv = pr.NO / max(1, tv.sum())
+    sb = pr.NG / max(1, tb.sum())
+    t_a = timed(lambda: far(pr.vol, pr.bnd)) + sb * timed(lambda: f.p2p(q, pr.vol, tb))
+    t_b = timed(lambda: far(pr.bnd, pr.bnd)) + sb * timed(lambda: f.p2p(q, pr.bnd, tb))
+    t_c = timed(lambda: far(pr.vol | pr.bnd, pr.vol)) + sv * timed(lambda: f.p2p(q, pr.vol | pr.bnd, tv))
+    t_fdm = timed(lambda: fdm.fdm_apply(q[:pr.NO], w["n"], w["k"]))
+    per_apply = t_a + inner_per_apply * t_b + t_c
+    per_solve = outer_iters * (per_apply + t_fdm)
+    desc = (f"oracle FMM passes at {w['n']}^3 (A: vol->bnd, B: bnd->bnd, C: all->vol): far field in "
+            f"full, P2P for targets in {len(pick)}/{len(leaves)} random leaves scaled by point "
+            f"fraction; per solve = {outer_iters} x (A + {inner_per_apply:.1f} B + C + FDM); "
+            f"sample wall {time.perf_counter() - t0:.1f} s")
+    return per_solve, desc
+
+
+def torch_threads():
+    try:
+        import torch
+        return torch.get_num_threads()
+    except Exception:
+        return os.cpu_count()
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args, world, rank):
+    """The oracle alone on the host: each step times a bounded sample of the
+    same workload scaled to one solve.  The iteration counts come from the
+    oracle's own recorded solve when present, else from the paper-free default
+    (one outer iteration per step)."""
+    if rank != 0:
+        return
+    from paper_1608_02461_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    golden = os.path.join(ROOT, "tests", "golden", f"oracle_{args.workload}.json")
+    if os.path.exists(golden):
+        g = json.load(open(golden))
+        outer, inner = g["iters"], g["inner_iters_total"] / max(1, g["iters"])
+        basis = "iteration counts of the oracle's recorded FP64 solve"
+    else:
+        outer, inner = 1, 10.0
+        basis = "one outer iteration with 10 inner iterations (no recorded oracle solve)"
+    times = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, desc = oracle_sample(w, inner, outer)
+        if i >= args.warmup:
+            times.append(v)
+    val = float(np.mean(times))
+    cores = torch_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, **{k: w[k] for k in ("n", "k", "p", "leaf", "theta")}},
+            "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle",
+                             "sample": desc + "; " + basis},
+            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_1608_02461_gb300 import hfmm, inputs
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    w = inputs.WORKLOADS[args.workload]
+    n = w["n"]
+    gm = dict(restart=w["restart"], rtol=1e-6, inner_rtol=args.inner_rtol, inner_maxit=200, inner_m=50)
+
+    t0 = time.perf_counter()
+    tree = hfmm.Tree(n, w["k"], w["p"], w["theta"], w["leaf"], args.precision)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    b_host = inputs.workload_rhs(args.workload)
+    b = torch.from_numpy(b_host).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        x, info = tree.gmres(b, **gm)
+        return x, info
+
+    for _ in range(args.warmup):
+        x, info = solve()
+    assert info.status == 0, f"warm-up solve did not converge: {info}"
+
+    clocks = ClockSampler(not args.no_clocks and rank == 0, local)
+    tree.set_timing(True)
+    launches0 = tree.stats().launches
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    infos = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                      # evict L2 between steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = solve()
+        e1.record(stream)
+        evs.append((e0, e1))
+        infos.append(info)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    st = tree.stats()
+    launches = st.launches - launches0
+    stages = tree.stage_times()
+    tree.set_timing(False)
+    ms = sum(a.elapsed_time(c) for a, c in evs) / args.steps
+    ms = barrier_max(ms, world, dev)
+    info = infos[-1]
+    relres = info.relres_true
+
+    # dominant stage and its roofline
+    dom = max(("p2p", "m2l", "p2m", "l2p", "m2m", "l2l", "gather", "fdm"), key=lambda s: stages[s][0])
+    sm_, nl_, work_ = stages[dom]
+    peaks, peak_kind = measured_peaks()
+    if dom == "p2p":
+        flop = work_ * P2P_FLOP_PER_PAIR
+        achieved = flop / (sm_ * 1e-3) / 1e12
+        peak = FP32_ALU_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "kernel": "k_p2p", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "per_launch_ms": sm_ / max(1, nl_), "work_per_launch": work_ / max(1, nl_),
+                "work_unit": "point pairs", "gpair_s": work_ / (sm_ * 1e-3) / 1e9,
+                "peak_source": "FP32 lanes x clock (152 SM x 128 x 2 x 2.07 GHz)" if args.precision == "fp32"
+                else "nominal FP64 rate"}
+    elif dom == "m2l":
+        achieved = work_ / (sm_ * 1e-3) / 1e12
+        peak = FP32_ALU_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "kernel": "k_m2l", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "per_launch_ms": sm_ / max(1, nl_),
+                "work_per_launch": work_ / max(1, nl_), "work_unit": "flop (8 p^4 per cell pair)"}
+    else:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None}
+    roof["peak_kind"] = peak_kind if roof["bound"] == "hbm" else "derived"
+    stage_summary = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(1, args.steps)}
+                     for k, v in stages.items()}
+
+    # FMM apply throughput (full apply, all points sources and targets)
+    qv = torch.from_numpy(inputs.complex_normal(n ** 3, 51)).to(dev)
+    qb = torch.from_numpy(inputs.complex_normal(6 * n * n, 52)).to(dev)
+    pv, pb = tree.apply(qv, qb)
+    torch.cuda.synchronize()
+    reps = 5
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    app_ms = 0.0
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0.record(stream)
+        tree.apply(qv, qb, phi_vol=pv, phi_bnd=pb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        app_ms += e0.elapsed_time(e1)
+    app_ms /= reps
+    mpts = (n ** 3 + 6 * n * n) / (app_ms * 1e-3) / 1e6
+
+    # end to end through host buffers
+    b_pin = torch.from_numpy(b_host).pin_memory()
+    x_pin = torch.empty_like(b_pin).pin_memory()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        bd = b_pin.to(dev, non_blocking=True)
+        xd, _ = tree.gmres(bd, **gm)
+        x_pin.copy_(xd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms /= args.steps
+    e2e_ms = barrier_max(e2e_ms, world, dev)
+    nbytes = b_pin.numel() * b_pin.element_size()
+
+    # plain FP64 form of the same solve
+    fp64 = None
+    if not args.no_fp64 and args.precision == "fp32":
+        t64 = hfmm.Tree(n, w["k"], w["p"], w["theta"], w["leaf"], "fp64")
+        t64.gmres(b, **gm)          # warm-up
+        flush.fill_(1.0)
+        e0.record(stream)
+        _, i64 = t64.gmres(b, **gm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64 = {"time_to_solution_s": e0.elapsed_time(e1) * 1e-3, "gmres_iters": i64.iters,
+                "inner_iters_total": i64.inner_iters_total, "relres_true": i64.relres_true,
+                "iters_ratio_fp32_over_fp64": info.iters / max(1, i64.iters)}
+        t64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        inner = info.inner_iters_total / max(1, info.iters)
+        v, desc = oracle_sample(w, inner, info.iters)
+        cpu = {"value": v, "unit": "s", "cores": torch_threads(), "kind": "oracle",
+               "sample": desc + "; iteration counts of this run's solve"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "k": w["k"], "p": w["p"], "leaf": w["leaf"],
+                       "theta": w["theta"], "restart": w["restart"], "inner_rtol": args.inner_rtol,
+                       "fmm_precision": args.precision, "krylov_precision": "fp64",
+                       "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gmres_iters": info.iters, "inner_iters_total": info.inner_iters_total,
+            "relres_true": relres, "build_s": build_s,
+            "solves_per_s": world / (ms * 1e-3),
+            "fmm_apply_ms": app_ms, "fmm_apply_mpts_s": mpts,
+            "gpu_launches": int(launches),
+            "roofline": roof, "stages_per_solve": stage_summary,
+            "e2e": {"value": e2e_ms * 1e-3, "unit": "s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "fp64": fp64, "cpu_baseline": cpu, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    tree.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

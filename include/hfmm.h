@@ -89,6 +89,17 @@ typedef struct hfmm_gmres_info {
     int history_len;
 } hfmm_gmres_info;
 
+/* stages timed by fmm_set_timing (index into hfmm_stats.stage_ms) */
+#define HFMM_STAGE_GATHER  0  /* input permutation into leaf order, output scatter */
+#define HFMM_STAGE_P2M     1
+#define HFMM_STAGE_M2M     2
+#define HFMM_STAGE_M2L     3
+#define HFMM_STAGE_L2L     4
+#define HFMM_STAGE_L2P     5
+#define HFMM_STAGE_P2P     6  /* near field and self term                    */
+#define HFMM_STAGE_FDM     7  /* 7-point operator inside gmres_solve         */
+#define HFMM_NSTAGES       8
+
 typedef struct hfmm_stats {
     int L;                 /* tree depth                                   */
     int p;
@@ -98,6 +109,13 @@ typedef struct hfmm_stats {
     int64_t p2p_pairs;     /* near-field point pairs, all points as sources and targets */
     int64_t device_bytes;  /* device memory held by the handle              */
     double ms_last_apply;  /* CUDA-event time of the last fmm_apply/precond */
+    int64_t launches;      /* kernels this library has launched in this process */
+    double stage_ms[HFMM_NSTAGES];     /* CUDA-event time per stage since timing
+                                          was switched on (fmm_set_timing)      */
+    int64_t stage_launches[HFMM_NSTAGES]; /* kernel launches per stage, same span */
+    double stage_work[HFMM_NSTAGES];   /* algorithmic work per stage, same span:
+                                          P2P point pairs (j != i), M2L flops
+                                          (8 p^4 per cell pair), 0 elsewhere   */
 } hfmm_stats;
 
 typedef struct fmm_tree fmm_tree;
@@ -197,8 +215,17 @@ int hfmm_fdm_apply(fmm_tree* tree, const void* d_u, void* d_out, void* stream);
 int gmres_solve(fmm_tree* tree, const void* d_b, void* d_x,
                 const hfmm_gmres_params* gp, hfmm_gmres_info* info, void* stream);
 
-/* Sizes and counters of a built tree. */
+/* Sizes and counters of a built tree.  Waits for the handle's pending
+ * timing events (host blocks until they complete). */
 int fmm_get_stats(const fmm_tree* tree, hfmm_stats* stats);
+
+/*
+ * fmm_set_timing -- switch per-stage CUDA-event timing on (1) or off (0) for
+ * the handle and reset the stage accumulators.  While on, every stage launch
+ * is bracketed by events on the launching stream; fmm_get_stats resolves
+ * them.  Costs two event records per stage and no synchronisation.
+ */
+int fmm_set_timing(fmm_tree* tree, int enable);
 
 #ifdef __cplusplus
 }

@@ -3,6 +3,7 @@
 // preconditioned GMRES (Sec. 3-4, Sec. 6).
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "krylov.cuh"
@@ -36,11 +37,17 @@ void release(fmm_tree* t) {
   t->bufs.clear();
   if (t->ev0) cudaEventDestroy(t->ev0);
   if (t->ev1) cudaEventDestroy(t->ev1);
+  t->timer.destroy();
 }
 
 fmm_tree_ext* ext_of(fmm_tree* t) { return t->ext; }
 
+std::atomic<int64_t> g_launches{0};
+
 }  // namespace
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 int tree_alloc(fmm_tree* t, void** ptr, size_t bytes) {
   *ptr = nullptr;
@@ -79,6 +86,9 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   }
   t->level_off[t->L + 1] = off;
   t->total_cells = off;
+  HFMM_TRY(tree_alloc_t(t, &t->level_off_dev, HFMM_MAX_LEVEL + 2));
+  HFMM_CUDA_TRY(cudaMemcpyAsync(t->level_off_dev, t->level_off, sizeof(t->level_off),
+                                cudaMemcpyHostToDevice, s));
   const int64_t nleaf = (int64_t)1 << (3 * t->L);
   const int64_t N = t->n_pts;
   HFMM_TRY(tree_alloc_t(t, &t->xyz, 3 * N));
@@ -93,6 +103,8 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   HFMM_TRY(tree_alloc(t, &t->Lc, csz * t->total_cells * P));
   HFMM_TRY(tree_alloc(t, &t->qs, csz * N));
   HFMM_TRY(tree_alloc(t, &t->phis, csz * N));
+  t->m2l_part_max = 8;
+  HFMM_TRY(tree_alloc(t, &t->m2l_part, csz * t->total_cells * P * t->m2l_part_max));
   HFMM_TRY(tree_alloc_t(t, &t->g_bnd, t->n_bnd + 1));
   HFMM_TRY(tree_alloc_t(t, &t->q_bnd, t->n_bnd + 1));
   HFMM_CUDA_TRY(cudaMemsetAsync(t->M, 0, csz * t->total_cells * P, s));
@@ -101,6 +113,8 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   HFMM_TRY(build_lists(t, s));
   HFMM_TRY(build_self_terms(t, s));
   HFMM_TRY(build_operators(t, s));
+  HFMM_TRY(build_pair_counts(t, s));
+  HFMM_TRY(build_m2l_tiles(t, s));
   HFMM_CUDA_TRY(cudaEventCreate(&t->ev0));
   HFMM_CUDA_TRY(cudaEventCreate(&t->ev1));
   HFMM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -229,6 +243,7 @@ static int precond_impl(fmm_tree* t, const double2* r, double2* z, double inner_
   HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, r, h3, t->q_bnd, h2, s));
   HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, s));
   HFMM_TRY(fmm_scatter(t, HFMM_SET_VOL, z, nullptr, s));
+  if (fmm_device_error(s, true)) return HFMM_ERR_TIMEOUT;
   return HFMM_OK;
 }
 
@@ -263,7 +278,10 @@ extern "C" int gmres_solve(fmm_tree* t, const void* d_b, void* d_x, const hfmm_g
   const int64_t N = t->n_vol;
   HFMM_TRY(gmres_work_reserve(e->outer, N, gp->restart_m, true));
   DevOp A = [t, s](const double2* in, double2* out) -> int {
-    return fdm_apply_dev(t->n, t->h, t->k, in, out, s);
+    t->timer.begin(HFMM_STAGE_FDM, s);
+    int st = fdm_apply_dev(t->n, t->h, t->k, in, out, s);
+    t->timer.end(1, s);
+    return st;
   };
   int inner_total = 0;
   DevOp M = [t, gp, s, &inner_total](const double2* in, double2* out) -> int {
@@ -305,5 +323,19 @@ extern "C" int fmm_get_stats(const fmm_tree* t, hfmm_stats* st) {
   else
     cudaGetLastError();
   st->ms_last_apply = tt->ms_last_apply;
+  tt->timer.flush();
+  st->launches = launches_so_far();
+  for (int i = 0; i < HFMM_NSTAGES; ++i) {
+    st->stage_ms[i] = tt->timer.ms[i];
+    st->stage_launches[i] = tt->timer.launches[i];
+    st->stage_work[i] = tt->timer.work[i];
+  }
+  return HFMM_OK;
+}
+
+extern "C" int fmm_set_timing(fmm_tree* t, int enable) {
+  if (!t || (enable != 0 && enable != 1)) return HFMM_ERR_INVALID_ARG;
+  t->timer.reset();
+  t->timer.on = enable != 0;
   return HFMM_OK;
 }

@@ -16,6 +16,9 @@
 namespace {
 
 template <typename T>
+int set_smem(const void* fn, size_t bytes);
+
+template <typename T>
 struct FmmDev {
   const double* xyz;     // sorted coordinates, FP64
   const float4* xyz32;   // sorted coordinates relative to their leaf centre, FP32
@@ -135,11 +138,12 @@ __global__ void k_p2m(FmmDev<T> d, int64_t leaf_off, int src_set, int chunk) {
 }
 
 // ---------------------------------------------------------------- M2M / L2L
-// out[a'] (+)= sum_a T[a'][a] in[a]; thread per a' (a' = tid + s*blockDim)
+// out[a'] = sum_a T(a', a) in[a] with T column-major (entry (a', a) at a*P + a');
+// one thread per a', so a warp reads consecutive words of each column
 template <typename T>
-__device__ __forceinline__ C<T> matvec_row(const C<T>* Trow, const C<T>* x, int P) {
+__device__ __forceinline__ C<T> matvec_row(const C<T>* Tcol, int ap, const C<T>* x, int P) {
   C<T> acc = mkc<T>(0, 0);
-  for (int a = 0; a < P; ++a) cfma<T>(acc, Trow[a], x[a]);
+  for (int a = 0; a < P; ++a) cfma<T>(acc, Tcol[(int64_t)a * P + ap], x[a]);
   return acc;
 }
 
@@ -160,8 +164,7 @@ __global__ void k_m2m(FmmDev<T> d, int level, int64_t off_par, int64_t off_child
   for (int ap = threadIdx.x; ap < P; ap += blockDim.x) {
     C<T> acc = mkc<T>(0, 0);
     for (int o = 0; o < 8; ++o) {
-      const C<T>* Trow = ops + ((int64_t)o * P + ap) * P;
-      C<T> v = matvec_row<T>(Trow, xs + o * P, P);
+      C<T> v = matvec_row<T>(ops + (int64_t)o * P * P, ap, xs + o * P, P);
       acc = cadd<T>(acc, v);
     }
     Mp[ap] = acc;
@@ -180,7 +183,7 @@ __global__ void k_l2l(FmmDev<T> d, int64_t off_par, int64_t off_child, const C<T
   __syncthreads();
   C<T>* Lch = d.Lc + (off_child + cell) * P;
   for (int ap = threadIdx.x; ap < P; ap += blockDim.x) {
-    C<T> v = matvec_row<T>(ops + ((int64_t)o * P + ap) * P, xs, P);
+    C<T> v = matvec_row<T>(ops + (int64_t)o * P * P, ap, xs, P);
     Lch[ap] = cadd<T>(Lch[ap], v);
   }
 }
@@ -214,13 +217,413 @@ __global__ void k_m2l(FmmDev<T> d, int level, int64_t off, const C<T>* ops, cons
     const C<T>* Top = ops + (int64_t)m2l_slot[b * m2l_count + i] * P * P;
     for (int q = 0; q < 4; ++q) {
       int ap = threadIdx.x + q * blockDim.x;
-      if (ap < P) acc[q] = cadd<T>(acc[q], matvec_row<T>(Top + (int64_t)ap * P, xs, P));
+      if (ap < P) acc[q] = cadd<T>(acc[q], matvec_row<T>(Top, ap, xs, P));
     }
   }
   for (int q = 0; q < 4; ++q) {
     int ap = threadIdx.x + q * blockDim.x;
     if (ap < P) d.Lc[(off + cell) * P + ap] = acc[q];
   }
+}
+
+// Tiled M2L over all levels in one launch.  A block owns a tile of TC target
+// cells of one level and parity class (so they share their offset list); for
+// each offset it stages the operator (P x P, column-major) and the TC source
+// expansions in shared memory and forms the P x TC complex product with a
+// register tile of R rows x CM columns per thread (128 threads as 16 row
+// groups x 8 column groups).  Offsets whose sources hold no point of the
+// source set in the whole tile are skipped.
+template <typename T, int R, int CM>
+__global__ void __launch_bounds__(128) k_m2l_tiled(FmmDev<T> d, const int4* __restrict__ tiles,
+                                                   const int* __restrict__ cells,
+                                                   const int64_t* __restrict__ level_off,
+                                                   const C<T>* __restrict__ ops, int64_t box_cells,
+                                                   const int* __restrict__ m2l_off,
+                                                   const int* __restrict__ m2l_slot, int m2l_count,
+                                                   int src_set) {
+  constexpr int CT = 8, RT = 16, TC = CT * CM;
+  extern __shared__ unsigned char smem_raw[];
+  const int P = d.P;
+  C<T>* Ts = reinterpret_cast<C<T>*>(smem_raw);           // [P][P] column-major
+  C<T>* Ms = Ts + (size_t)P * P;                          // [P][TC + 1]
+  int* scell = reinterpret_cast<int*>(Ms + (size_t)P * (TC + 1));
+  int* tcell = scell + TC;
+  int* tco = tcell + TC;                                  // [TC][3] target coordinates
+  const int4 tile = tiles[blockIdx.x];
+  const int level = tile.x, b = tile.y, first = tile.z, cnt = tile.w;
+  const int64_t off = level_off[level];
+  const int s = 1 << level;
+  const int tid = threadIdx.x;
+  const int r0 = tid / CT, c0 = tid % CT;
+  if (tid < TC) {
+    int cell = tid < cnt ? cells[first + tid] : -1;
+    tcell[tid] = cell;
+    int ix = 0, iy = 0, iz = 0;
+    if (cell >= 0) morton_decode((uint64_t)cell, ix, iy, iz);
+    tco[3 * tid] = ix;
+    tco[3 * tid + 1] = iy;
+    tco[3 * tid + 2] = iz;
+  }
+  C<T> acc[R][CM];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = 0; j < CM; ++j) acc[r][j] = mkc<T>(0, 0);
+  const C<T>* opsl = ops + (int64_t)level * box_cells * P * P;
+  __syncthreads();
+  for (int i = 0; i < m2l_count; ++i) {
+    const int o = m2l_off[b * m2l_count + i];
+    bool valid = false;
+    if (tid < TC) {
+      int src = -1;
+      if (tcell[tid] >= 0) {
+        int jx = tco[3 * tid] + (o & 255) - 128, jy = tco[3 * tid + 1] + ((o >> 8) & 255) - 128,
+            jz = tco[3 * tid + 2] + ((o >> 16) & 255) - 128;
+        if (jx >= 0 && jy >= 0 && jz >= 0 && jx < s && jy < s && jz < s) {
+          int c = (int)morton_encode(jx, jy, jz);
+          if (d.flags[off + c] & src_set) src = c;
+        }
+      }
+      scell[tid] = src;
+      valid = src >= 0;
+    }
+    if (!__syncthreads_or(valid)) continue;
+    const C<T>* Top = opsl + (int64_t)m2l_slot[b * m2l_count + i] * P * P;
+    for (int e = tid; e < P * P; e += 128) Ts[e] = Top[e];
+    for (int e = tid; e < P * TC; e += 128) {
+      int c = e / P, a = e - c * P;
+      int sc = scell[c];
+      Ms[a * (TC + 1) + c] = sc >= 0 ? d.M[(off + sc) * P + a] : mkc<T>(0, 0);
+    }
+    __syncthreads();
+    for (int a = 0; a < P; ++a) {
+      C<T> tv[R], mv[CM];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        int ap = r0 + r * RT;
+        tv[r] = ap < P ? Ts[a * P + ap] : mkc<T>(0, 0);
+      }
+#pragma unroll
+      for (int j = 0; j < CM; ++j) mv[j] = Ms[a * (TC + 1) + c0 + j * CT];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < CM; ++j) cfma<T>(acc[r][j], tv[r], mv[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = 0; j < CM; ++j) {
+      int ap = r0 + r * RT, c = c0 + j * CT;
+      if (ap < P && c < cnt) d.Lc[(off + tcell[c]) * P + ap] = acc[r][j];
+    }
+}
+
+// ---- TMA-staged, split-offset M2L (even p: rows are multiples of 16 bytes)
+//
+// Same tiling as k_m2l_tiled, but (1) the offsets of a tile whose sources hold
+// no point of the source set are dropped up front, (2) the operator and the
+// source rows of the next offset are fetched with 1D bulk copies
+// (cp.async.bulk, completion on an mbarrier) while the current one is
+// multiplied (two stages), and (3) a tile's offset list may be split over
+// gridDim.y blocks whose partial sums go to a scratch array, reduced in a
+// fixed order afterwards (deterministic).
+
+__device__ int g_fmm_error;  // set when a bounded wait gives up (HFMM_ERR_TIMEOUT)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: gives up (false) after one second of wall time
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (global_ns() - t0 < 1000000000ull)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename T, int R, int CM>
+__global__ void __launch_bounds__(128) k_m2l_tma(FmmDev<T> d, const int4* __restrict__ tiles,
+                                                 const int* __restrict__ cells,
+                                                 const int64_t* __restrict__ level_off,
+                                                 const C<T>* __restrict__ ops, int64_t box_cells,
+                                                 const int* __restrict__ m2l_off,
+                                                 const int* __restrict__ m2l_slot, int m2l_count,
+                                                 int src_set, C<T>* __restrict__ part, int64_t part_stride) {
+  constexpr int CT = 8, RT = 16, TC = CT * CM;
+  const int P = d.P;
+  const int MS = P + 2;  // padded source row (16-byte multiple, spreads banks)
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);                  // [2]
+  int* vlist = reinterpret_cast<int*>(smem_raw + 16);                     // [m2l_count] valid offsets
+  unsigned* vmask = reinterpret_cast<unsigned*>(vlist + m2l_count);       // [m2l_count] column masks
+  int* tcell = reinterpret_cast<int*>(vmask + m2l_count);                 // [TC]
+  int* tco = tcell + TC;                                                  // [TC][3]
+  int* nval = tco + 3 * TC;                                               // [1]
+  size_t hdr = 16 + sizeof(int) * (2 * (size_t)m2l_count + 4 * TC + 4);
+  hdr = (hdr + 127) & ~(size_t)127;
+  C<T>* Ts = reinterpret_cast<C<T>*>(smem_raw + hdr);                    // [2][P*P]
+  C<T>* Ms = Ts + 2 * (size_t)P * P;                                      // [2][TC][MS]
+
+  const int4 tile = tiles[blockIdx.x];
+  const int level = tile.x, b = tile.y, first = tile.z, cnt = tile.w;
+  const int64_t off = level_off[level];
+  const int s = 1 << level;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = tid / CT, c0 = tid % CT;
+  if (tid < TC) {
+    int cell = tid < cnt ? cells[first + tid] : -1;
+    tcell[tid] = cell;
+    int ix = 0, iy = 0, iz = 0;
+    if (cell >= 0) morton_decode((uint64_t)cell, ix, iy, iz);
+    tco[3 * tid] = ix;
+    tco[3 * tid + 1] = iy;
+    tco[3 * tid + 2] = iz;
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // valid offsets and their column masks (one warp per offset, lane = column)
+  for (int i = warp; i < m2l_count; i += 4) {
+    const int o = m2l_off[b * m2l_count + i];
+    bool v = false;
+    if (lane < TC && tcell[lane] >= 0) {
+      int jx = tco[3 * lane] + (o & 255) - 128, jy = tco[3 * lane + 1] + ((o >> 8) & 255) - 128,
+          jz = tco[3 * lane + 2] + ((o >> 16) & 255) - 128;
+      if (jx >= 0 && jy >= 0 && jz >= 0 && jx < s && jy < s && jz < s)
+        v = (d.flags[off + morton_encode(jx, jy, jz)] & src_set) != 0;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, v);
+    if (lane == 0) vmask[i] = m;
+  }
+  __syncthreads();
+  if (tid == 0) {  // compact in offset order
+    int n = 0;
+    for (int i = 0; i < m2l_count; ++i)
+      if (vmask[i]) {
+        vmask[n] = vmask[i];
+        vlist[n++] = i;
+      }
+    *nval = n;
+  }
+  __syncthreads();
+  const int nv = *nval;
+  // this block's share of the valid offsets
+  const int ks = blockIdx.y, kn = gridDim.y;
+  const int sbeg = (int)((int64_t)nv * ks / kn), send = (int)((int64_t)nv * (ks + 1) / kn);
+  const C<T>* opsl = ops + (int64_t)level * box_cells * P * P;
+  const uint32_t op_bytes = (uint32_t)((size_t)P * P * sizeof(C<T>));
+  const uint32_t row_bytes = (uint32_t)((size_t)P * sizeof(C<T>));
+
+  // warp 0 issues the copies of step `st` into stage (st - sbeg) & 1
+  auto issue = [&](int st) {
+    const int i = vlist[st];
+    const unsigned m = vmask[st];
+    const int stg = (st - sbeg) & 1;
+    if (lane == 0) {
+      fence_async_shared();
+      mbar_expect_tx(&bar[stg], op_bytes + (uint32_t)__popc(m) * row_bytes);
+    }
+    __syncwarp();
+    if (lane == 0)
+      bulk_copy_g2s(Ts + (size_t)stg * P * P, opsl + (int64_t)m2l_slot[b * m2l_count + i] * P * P, op_bytes,
+                    &bar[stg]);
+    if (lane < TC && (m >> lane) & 1u) {
+      const int o = m2l_off[b * m2l_count + i];
+      int jx = tco[3 * lane] + (o & 255) - 128, jy = tco[3 * lane + 1] + ((o >> 8) & 255) - 128,
+          jz = tco[3 * lane + 2] + ((o >> 16) & 255) - 128;
+      int64_t src = (int64_t)morton_encode(jx, jy, jz);
+      bulk_copy_g2s(Ms + ((size_t)stg * TC + lane) * MS, d.M + (off + src) * P, row_bytes, &bar[stg]);
+    }
+  };
+
+  C<T> acc[R][CM];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = 0; j < CM; ++j) acc[r][j] = mkc<T>(0, 0);
+
+  if (warp == 0 && sbeg < send) issue(sbeg);
+  int failed_at = -1;
+  for (int st = sbeg; st < send; ++st) {
+    const int stg = (st - sbeg) & 1;
+    if (warp == 0 && st + 1 < send) issue(st + 1);
+    const uint32_t parity = (uint32_t)(((st - sbeg) >> 1) & 1);
+    bool ok = mbar_wait_bounded(&bar[stg], parity);
+    if (__syncthreads_or(!ok)) {
+      failed_at = st;
+      break;
+    }
+    const unsigned m = vmask[st];
+    bool cv[CM];
+#pragma unroll
+    for (int j = 0; j < CM; ++j) cv[j] = (m >> (c0 + j * CT)) & 1u;
+    const C<T>* Tst = Ts + (size_t)stg * P * P;
+    const C<T>* Mst = Ms + (size_t)stg * TC * MS;
+    for (int a = 0; a < P; ++a) {
+      C<T> tv[R], mv[CM];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        int ap = r0 + r * RT;
+        tv[r] = ap < P ? Tst[a * P + ap] : mkc<T>(0, 0);
+      }
+#pragma unroll
+      for (int j = 0; j < CM; ++j) {
+        C<T> v = Mst[(c0 + j * CT) * MS + a];
+        mv[j] = cv[j] ? v : mkc<T>(0, 0);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < CM; ++j) cfma<T>(acc[r][j], tv[r], mv[j]);
+    }
+    __syncthreads();  // stage free for the copy issued in the next step
+  }
+  if (failed_at >= 0) {
+    // record the error, then give the copies still in flight (the step that
+    // timed out and the one issued after it) a bounded time to land before
+    // the block's shared memory is released
+    if (tid == 0) {
+      atomicExch(&g_fmm_error, HFMM_ERR_TIMEOUT);
+      for (int st = failed_at; st < send && st <= failed_at + 1; ++st)
+        mbar_wait_bounded(&bar[(st - sbeg) & 1], (uint32_t)(((st - sbeg) >> 1) & 1));
+    }
+    __syncthreads();
+    return;
+  }
+  C<T>* out = part ? part + (int64_t)ks * part_stride : nullptr;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = 0; j < CM; ++j) {
+      int ap = r0 + r * RT, c = c0 + j * CT;
+      if (ap < P && c < cnt) {
+        if (out)
+          out[(int64_t)(first + c) * P + ap] = acc[r][j];
+        else
+          d.Lc[(off + tcell[c]) * P + ap] = acc[r][j];
+      }
+    }
+}
+
+// L of every tile cell = sum over the split parts, in part order
+template <typename T>
+__global__ void k_m2l_reduce(FmmDev<T> d, const int4* __restrict__ tiles, const int* __restrict__ cells,
+                             const int64_t* __restrict__ level_off, const C<T>* __restrict__ part,
+                             int64_t part_stride, int nsplit) {
+  const int4 tile = tiles[blockIdx.x];
+  const int P = d.P;
+  const int64_t off = level_off[tile.x];
+  for (int e = threadIdx.x; e < tile.w * P; e += blockDim.x) {
+    int c = e / P, a = e - c * P;
+    int64_t slot = (int64_t)(tile.z + c) * P + a;
+    C<T> v = part[slot];
+    for (int k = 1; k < nsplit; ++k) v = cadd<T>(v, part[k * part_stride + slot]);
+    d.Lc[(off + cells[tile.z + c]) * P + a] = v;
+  }
+}
+
+template <typename T, int CM>
+int launch_m2l_tma(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
+                   cudaStream_t s) {
+  const int P = t->P, mi = tgt_set - 1;
+  const int TC = 8 * CM;
+  const int nt = t->m2l_ntiles[mi];
+  if (nt == 0) return HFMM_OK;
+  size_t hdr = 16 + sizeof(int) * (2 * (size_t)t->m2l_count + 4 * TC + 4);
+  hdr = (hdr + 127) & ~(size_t)127;
+  size_t sm = hdr + (2 * (size_t)P * P + 2 * (size_t)TC * (P + 2)) * sizeof(C<T>);
+  // split the offset lists so that the grid fills the GPU a few times over
+  int nsplit = (4 * 152 + nt - 1) / nt;
+  if (nsplit > t->m2l_part_max) nsplit = t->m2l_part_max;
+  if (nsplit < 1) nsplit = 1;
+  C<T>* part = nsplit > 1 ? reinterpret_cast<C<T>*>(t->m2l_part) : nullptr;
+  const int64_t pstride = t->total_cells * (int64_t)P;
+  const int R = (P + 15) / 16;
+  dim3 grid(nt, nsplit);
+#define HFMM_M2L_TMA_CASE(RR)                                                               \
+  if (R <= RR) {                                                                            \
+    HFMM_TRY(set_smem<T>((const void*)k_m2l_tma<T, RR, CM>, sm));                           \
+    k_m2l_tma<T, RR, CM><<<grid, 128, sm, s>>>(d, t->m2l_tiles[mi], t->m2l_cells[mi],       \
+                                               t->level_off_dev, ops, t->box_cells,         \
+                                               t->m2l_off, t->m2l_box_index, t->m2l_count,  \
+                                               src_set, part, pstride);                     \
+    if (nsplit > 1)                                                                         \
+      k_m2l_reduce<T><<<nt, 128, 0, s>>>(d, t->m2l_tiles[mi], t->m2l_cells[mi],             \
+                                         t->level_off_dev, part, pstride, nsplit);          \
+    count_launches(nsplit > 1 ? 2 : 1);                                                     \
+    return hfmm_last_launch();                                                              \
+  }
+  HFMM_M2L_TMA_CASE(1)
+  HFMM_M2L_TMA_CASE(2)
+  HFMM_M2L_TMA_CASE(3)
+  HFMM_M2L_TMA_CASE(4)
+  HFMM_M2L_TMA_CASE(6)
+#undef HFMM_M2L_TMA_CASE
+  return HFMM_ERR_UNSUPPORTED;
+}
+
+template <typename T, int CM>
+int launch_m2l_tiled(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, const int64_t* level_off_dev,
+                     int src_set, int tgt_set, cudaStream_t s) {
+  const int P = t->P, mi = tgt_set - 1;
+  const int TC = 8 * CM;
+  size_t sm = ((size_t)P * P + (size_t)P * (TC + 1)) * sizeof(C<T>) + 5 * TC * sizeof(int);
+  const int R = (P + 15) / 16;
+  const void* fn = nullptr;
+#define HFMM_M2L_CASE(RR)                                               \
+  if (R <= RR) {                                                        \
+    fn = (const void*)k_m2l_tiled<T, RR, CM>;                           \
+    HFMM_TRY(set_smem<T>(fn, sm));                                      \
+    k_m2l_tiled<T, RR, CM><<<t->m2l_ntiles[mi], 128, sm, s>>>(          \
+        d, t->m2l_tiles[mi], t->m2l_cells[mi], level_off_dev, ops, t->box_cells, t->m2l_off, \
+        t->m2l_box_index, t->m2l_count, src_set);                       \
+    return hfmm_last_launch();                                          \
+  }
+  HFMM_M2L_CASE(1)
+  HFMM_M2L_CASE(2)
+  HFMM_M2L_CASE(3)
+  HFMM_M2L_CASE(4)
+  HFMM_M2L_CASE(6)
+#undef HFMM_M2L_CASE
+  return HFMM_ERR_UNSUPPORTED;
 }
 
 // ---------------------------------------------------------------- L2P
@@ -367,6 +770,185 @@ __global__ void k_p2p(FmmDev<T> d, const int* near_off, int near_count, int src_
   }
 }
 
+// P2P, second form.  One block of 256 threads per target leaf.  The sources
+// of all near leaves are staged in shared memory in windows of up to W
+// points (coordinates relative to the target leaf centre, weights scaled by
+// 1/(4 pi)); each target is served by `tpt` threads (a power of two chosen so
+// that targets x tpt fills the block), each summing a strided share of the
+// window, and the shares are combined with warp shuffles.  A source at zero
+// distance from the target is the target itself (points are distinct) and
+// contributes nothing.  Window sums are added with Kahan compensation.
+template <typename T>
+struct StagedSrc {
+  T x, y, z, pad;
+};
+
+template <typename T>
+__device__ __forceinline__ void sincos_kr(T ph, T& sn, T& cs) {
+  if constexpr (sizeof(T) == 8) {
+    sincos(ph, &sn, &cs);
+  } else {
+    // reduce to [-pi, pi] (one-constant Cody-Waite step), then the SFU
+    const float n = rintf(ph * 0.15915494309189535f);
+    const float r = fmaf(-n, 6.28318530717958648f, ph);
+    sn = __sinf(r);
+    cs = __cosf(r);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T x) {
+  if constexpr (sizeof(T) == 8) return rsqrt(x);
+  else return rsqrtf(x);
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restrict__ near_off,
+                                                int near_count, int src_set, int tgt_set,
+                                                double2 sig_vol, double2 sig_bnd) {
+  __shared__ StagedSrc<T> spos[W];
+  __shared__ C<T> sq[W];
+  __shared__ int nb_leaf[128], nb_lo[128], nb_cnt[128], nb_pre[129];
+  __shared__ T nb_sh[128][3];
+  __shared__ int n_nb;
+  const int leaf = blockIdx.x;
+  int tlo, thi;
+  leaf_range(d.leaf_start, d.leaf_mid, leaf, tgt_set, tlo, thi);
+  const int ntgt = thi - tlo;
+  if (ntgt <= 0) return;
+  const int tid = threadIdx.x;
+  int ix, iy, iz;
+  morton_decode((uint64_t)leaf, ix, iy, iz);
+  const int s = 1 << d.L;
+  const T w = T(ldexp(1.0, -d.L));
+  // near leaves with sources: ranges and prefix sums
+  if (tid < 32) {
+    int base = 0;
+    for (int c0 = 0; c0 < near_count; c0 += 32) {
+      int i = c0 + tid;
+      int cnt = 0, lo = 0, sl = 0, ox = 0, oy = 0, oz = 0;
+      if (i < near_count) {
+        int o = near_off[i];
+        ox = (o & 255) - 128;
+        oy = ((o >> 8) & 255) - 128;
+        oz = ((o >> 16) & 255) - 128;
+        int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+        if (jx >= 0 && jy >= 0 && jz >= 0 && jx < s && jy < s && jz < s) {
+          sl = (int)morton_encode(jx, jy, jz);
+          int hi;
+          leaf_range(d.leaf_start, d.leaf_mid, sl, src_set, lo, hi);
+          cnt = hi > lo ? hi - lo : 0;
+        }
+      }
+      unsigned has = __ballot_sync(0xffffffffu, cnt > 0);
+      int pos = base + __popc(has & ((1u << tid) - 1u));
+      int v = cnt;  // inclusive scan of counts over the compacted lanes
+      if (cnt > 0) {
+        nb_leaf[pos] = sl;
+        nb_lo[pos] = lo;
+        nb_cnt[pos] = cnt;
+        nb_sh[pos][0] = T(ox) * w;
+        nb_sh[pos][1] = T(oy) * w;
+        nb_sh[pos][2] = T(oz) * w;
+      }
+      (void)v;
+      base += __popc(has);
+    }
+    if (tid == 0) {
+      n_nb = base;
+      int run = 0;
+      for (int q = 0; q < base; ++q) {
+        nb_pre[q] = run;
+        run += nb_cnt[q];
+      }
+      nb_pre[base] = run;
+    }
+  }
+  __syncthreads();
+  const int nnb = n_nb;
+  const int total = nb_pre[nnb];
+  const T inv4pi = T(0.07957747154594766788);
+  const T k = d.k;
+  // threads per target
+  int tpt = 1;
+  while (tpt < 32 && (tpt * 2) * ntgt <= 256) tpt *= 2;
+  const int tslots = 256 / tpt;
+  const int sub = tid % tpt;
+  for (int tb = 0; tb < ntgt; tb += tslots) {
+    const int ti = tb + tid / tpt;
+    const bool active = ti < ntgt;
+    const int i = tlo + (active ? ti : 0);
+    T xi, yi, zi;
+    local_coords<T>(d, i, leaf, xi, yi, zi);
+    C<T> tot = mkc<T>(0, 0), comp = mkc<T>(0, 0);
+    for (int wb = 0; wb < total; wb += W) {
+      const int wn = min(W, total - wb);
+      __syncthreads();
+      for (int e = tid; e < wn; e += 256) {
+        const int g = wb + e;
+        int lo = 0, hi = nnb;  // leaf of staged source g: last q with nb_pre[q] <= g
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if (nb_pre[mid] <= g) lo = mid;
+          else hi = mid;
+        }
+        const int j = nb_lo[lo] + (g - nb_pre[lo]);
+        T lx, ly, lz;
+        local_coords<T>(d, j, nb_leaf[lo], lx, ly, lz);
+        StagedSrc<T> sp;
+        sp.x = lx + nb_sh[lo][0];
+        sp.y = ly + nb_sh[lo][1];
+        sp.z = lz + nb_sh[lo][2];
+        sp.pad = T(0);
+        spos[e] = sp;
+        sq[e] = cscale<T>(d.qs[j], inv4pi);
+      }
+      __syncthreads();
+      C<T> part = mkc<T>(0, 0);
+      if (active) {
+#pragma unroll 4
+        for (int e = sub; e < wn; e += tpt) {
+          const StagedSrc<T> sp = spos[e];
+          const T dx = xi - sp.x, dy = yi - sp.y, dz = zi - sp.z;
+          const T r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+          T rinv = rsqrt_t<T>(r2);
+          rinv = r2 > T(0) ? rinv : T(0);
+          const T r = r2 * rinv;
+          T sn, cs;
+          sincos_kr<T>(k * r, sn, cs);
+          const C<T> q = sq[e];
+          const T wr = q.x * rinv, wi = q.y * rinv;
+          part.x = fma(cs, wr, fma(-sn, wi, part.x));
+          part.y = fma(cs, wi, fma(sn, wr, part.y));
+        }
+      }
+      if constexpr (sizeof(T) == 4) {
+        T yx = part.x - comp.x, yy = part.y - comp.y;
+        T tx = tot.x + yx, ty = tot.y + yy;
+        comp.x = (tx - tot.x) - yx;
+        comp.y = (ty - tot.y) - yy;
+        tot.x = tx;
+        tot.y = ty;
+      } else {
+        tot = cadd<T>(tot, part);
+      }
+    }
+    // combine the tpt shares (consecutive lanes of one warp)
+    for (int o = tpt >> 1; o > 0; o >>= 1) {
+      tot.x += __shfl_xor_sync(0xffffffffu, tot.x, o);
+      tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
+    }
+    if (active && sub == 0) {
+      const bool is_vol = i < d.leaf_mid[leaf];
+      if ((is_vol && (src_set & HFMM_SET_VOL)) || (!is_vol && (src_set & HFMM_SET_BND))) {
+        double2 sg = is_vol ? sig_vol : sig_bnd;
+        cfma<T>(tot, mkc<T>(T(sg.x), T(sg.y)), d.qs[i]);
+      }
+      d.phis[i] = cadd<T>(d.phis[i], tot);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- gather / scatter
 
 template <typename T>
@@ -450,31 +1032,80 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   const int64_t PP = (int64_t)P * P;
   const int th = threads_for(P);
 
+  StageTimer& tm = t->timer;
   // P2M
   const int chunk = 32;
   size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
   HFMM_TRY(set_smem<T>((const void*)k_p2m<T>, sm_p2m));
+  tm.begin(HFMM_STAGE_P2M, s);
   k_p2m<T><<<nleaf, 64, sm_p2m, s>>>(d, t->level_off[L], src_set, chunk);
+  tm.end(1, s);
+  count_launches(1);
   // M2M, levels L-1 .. 2
   size_t sm8 = 8 * (size_t)P * sizeof(C<T>);
   HFMM_TRY(set_smem<T>((const void*)k_m2m<T>, sm8));
-  for (int l = L - 1; l >= 2; --l)
-    k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1],
-                                            m2m + (int64_t)l * 8 * PP, src_set);
-  // M2L, levels 2 .. L
+  if (L > 2) {
+    tm.begin(HFMM_STAGE_M2M, s);
+    for (int l = L - 1; l >= 2; --l)
+      k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1],
+                                              m2m + (int64_t)l * 8 * PP, src_set);
+    tm.end(L - 2, s);
+    count_launches(L - 2);
+  }
+  // M2L, levels 2 .. L: tiled kernel in one launch when the operator fits in
+  // shared memory, else one launch per level of the per-cell kernel
   size_t sm1 = (size_t)P * sizeof(C<T>);
-  for (int l = 2; l <= L; ++l)
-    k_m2l<T><<<1 << (3 * l), th, sm1, s>>>(d, l, t->level_off[l], m2l + (int64_t)l * t->box_cells * PP,
-                                            t->m2l_off, t->m2l_box_index, t->m2l_count, src_set,
-                                            tgt_set);
+  tm.begin(HFMM_STAGE_M2L, s);
+  int nm2l = 0;
+  const bool tiled = (sizeof(T) == 4 && P <= 81) || (sizeof(T) == 8 && P <= 64);
+  const bool tma = tiled && ((size_t)P * sizeof(C<T>)) % 16 == 0;
+  if (tma) {
+    int st;
+    if (t->m2l_tc == 32)
+      st = launch_m2l_tma<T, 4>(t, d, m2l, src_set, tgt_set, s);
+    else
+      st = launch_m2l_tma<T, 2>(t, d, m2l, src_set, tgt_set, s);
+    HFMM_TRY(st);
+    nm2l = 0;  // counted by the launcher
+  } else if (tiled) {
+    int st;
+    if (t->m2l_tc == 32)  // tiles hold up to 32 cells: 8 column groups x 4
+      st = launch_m2l_tiled<T, 4>(t, d, m2l, t->level_off_dev, src_set, tgt_set, s);
+    else                  // 16 cells: 8 x 2
+      st = launch_m2l_tiled<T, 2>(t, d, m2l, t->level_off_dev, src_set, tgt_set, s);
+    HFMM_TRY(st);
+    nm2l = 1;
+  } else {
+    for (int l = 2; l <= L; ++l)
+      k_m2l<T><<<1 << (3 * l), th, sm1, s>>>(d, l, t->level_off[l], m2l + (int64_t)l * t->box_cells * PP,
+                                              t->m2l_off, t->m2l_box_index, t->m2l_count, src_set,
+                                              tgt_set);
+    nm2l = L - 1;
+  }
+  tm.end(nm2l > 0 ? nm2l : 1, s, tm.on ? m2l_work(t, src_set, tgt_set) : 0.0);
+  count_launches(nm2l);
   // L2L, levels 2 .. L-1 into their children
-  for (int l = 2; l < L; ++l)
-    k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1],
-                                                  l2l + (int64_t)l * 8 * PP, tgt_set);
+  if (L > 2) {
+    tm.begin(HFMM_STAGE_L2L, s);
+    for (int l = 2; l < L; ++l)
+      k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1],
+                                                    l2l + (int64_t)l * 8 * PP, tgt_set);
+    tm.end(L - 2, s);
+    count_launches(L - 2);
+  }
   // L2P then P2P (adds)
+  tm.begin(HFMM_STAGE_L2P, s);
   k_l2p<T><<<nleaf, 64, sm1, s>>>(d, t->level_off[L], tgt_set);
-  k_p2p<T><<<nleaf, 128, 0, s>>>(d, t->near_off, t->near_count, src_set, tgt_set, t->sigma_vol,
-                                  t->sigma_bnd);
+  tm.end(1, s);
+  tm.begin(HFMM_STAGE_P2P, s);
+  if (t->near_count <= 128)
+    k_p2p_v2<T, (sizeof(T) == 4 ? 1536 : 768)><<<nleaf, 256, 0, s>>>(
+        d, t->near_off, t->near_count, src_set, tgt_set, t->sigma_vol, t->sigma_bnd);
+  else
+    k_p2p<T><<<nleaf, 128, 0, s>>>(d, t->near_off, t->near_count, src_set, tgt_set, t->sigma_vol,
+                                    t->sigma_bnd);
+  tm.end(1, s, tm.on ? p2p_work(t, src_set, tgt_set) : 0.0);
+  count_launches(2);
   return hfmm_last_launch();
 }
 
@@ -483,13 +1114,27 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
 int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol, const double2* q_bnd,
                double scale_bnd, cudaStream_t s) {
   unsigned g = ceil_div(t->n_pts, 256);
+  t->timer.begin(HFMM_STAGE_GATHER, s);
   if (t->precision == HFMM_FP32)
     k_gather<float><<<g, 256, 0, s>>>(t->orig, t->n_pts, t->n_vol, src_set, q_vol, scale_vol, q_bnd,
                                       scale_bnd, reinterpret_cast<float2*>(t->qs));
   else
     k_gather<double><<<g, 256, 0, s>>>(t->orig, t->n_pts, t->n_vol, src_set, q_vol, scale_vol, q_bnd,
                                        scale_bnd, reinterpret_cast<double2*>(t->qs));
+  t->timer.end(1, s);
+  count_launches(1);
   return hfmm_last_launch();
+}
+
+int fmm_device_error(cudaStream_t s, bool clear) {
+  int h = 0;
+  HFMM_CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, g_fmm_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h && clear) {
+    int z = 0;
+    HFMM_CUDA_TRY(cudaMemcpyToSymbolAsync(g_fmm_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+  }
+  return h;
 }
 
 int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
@@ -499,11 +1144,14 @@ int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
 
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cudaStream_t s) {
   unsigned g = ceil_div(t->n_pts, 256);
+  t->timer.begin(HFMM_STAGE_GATHER, s);
   if (t->precision == HFMM_FP32)
     k_scatter<float><<<g, 256, 0, s>>>(t->pos_of, t->n_vol, t->n_bnd, tgt_set,
                                        reinterpret_cast<const float2*>(t->phis), phi_vol, phi_bnd);
   else
     k_scatter<double><<<g, 256, 0, s>>>(t->pos_of, t->n_vol, t->n_bnd, tgt_set,
                                         reinterpret_cast<const double2*>(t->phis), phi_vol, phi_bnd);
+  t->timer.end(1, s);
+  count_launches(1);
   return hfmm_last_launch();
 }

@@ -191,6 +191,7 @@ __global__ void k_backsolve(int kdim, int m, const double2* H, const double2* g,
 int fdm_apply_dev(int n, double h, double k, const double2* u, double2* out, cudaStream_t s) {
   int64_t N = (int64_t)n * n * n;
   k_fdm<<<ceil_div(N, 256), 256, 0, s>>>(n, 1.0 / (h * h), k * k, u, out);
+  count_launches(1);
   return hfmm_last_launch();
 }
 
@@ -245,6 +246,7 @@ void gmres_work_free(GmresWork& W) {
 int dev_norm(GmresWork& W, const double2* x, int64_t N, double* out_dev, cudaStream_t s) {
   k_norm_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, N, W.partial);
   k_norm_final<<<1, RED_THREADS, 0, s>>>(W.partial, RED_BLOCKS, out_dev);
+  count_launches(2);
   return hfmm_last_launch();
 }
 
@@ -252,6 +254,7 @@ static int mdot(GmresWork& W, const double2* V, int nvec, const double2* w, doub
   dim3 g(RED_BLOCKS, nvec);
   k_mdot_partial<<<g, RED_THREADS, 0, s>>>(V, W.N, nvec, w, W.N, (double2*)W.partial);
   k_mdot_final<<<nvec, RED_THREADS, 0, s>>>((double2*)W.partial, RED_BLOCKS, out);
+  count_launches(2);
   return hfmm_last_launch();
 }
 
@@ -281,6 +284,7 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
     } else {
       HFMM_TRY(A(x, W.w));
       k_sub<<<gN, 256, 0, s>>>(b, W.w, W.r, N);
+      count_launches(1);
     }
     HFMM_TRY(dev_norm(W, W.r, N, W.scal + 5, s));
     HFMM_CUDA_TRY(cudaMemcpyAsync(W.host, W.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -294,6 +298,7 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
     if (R.iters >= maxit) break;
     k_cycle_init<<<1, 64, 0, s>>>(m, W.scal + 5, W.g);
     k_scale_by<<<gN, 256, 0, s>>>(W.r, W.scal + 5, W.V, N);
+    count_launches(2);
     int jdone = 0;
     for (int j = 0; j < m; ++j) {
       double2* vj = W.V + (int64_t)j * N;
@@ -311,7 +316,11 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
       k_axpy_multi<<<gN, 256, 0, s>>>(W.V, N, j + 1, W.dots + (m + 1), -1.0, W.w, N);
       HFMM_TRY(dev_norm(W, W.w, N, W.scal + 1, s));
       k_arnoldi<<<1, 1, 0, s>>>(j, m, W.dots, W.H, W.cs, W.sn, W.g, W.scal);
-      if (j + 1 < m) k_scale_by<<<gN, 256, 0, s>>>(W.w, W.scal + 1, W.V + (int64_t)(j + 1) * N, N);
+      count_launches(3);
+      if (j + 1 < m) {
+        k_scale_by<<<gN, 256, 0, s>>>(W.w, W.scal + 1, W.V + (int64_t)(j + 1) * N, N);
+        count_launches(1);
+      }
       HFMM_TRY(hfmm_last_launch());
       HFMM_CUDA_TRY(cudaMemcpyAsync(W.host, W.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
       HFMM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -329,6 +338,7 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
     }
     k_backsolve<<<1, 1, 0, s>>>(jdone, m, W.H, W.g, W.y);
     k_axpy_multi<<<gN, 256, 0, s>>>(M ? W.Z : W.V, N, jdone, W.y, 1.0, x, N);
+    count_launches(2);
     HFMM_TRY(hfmm_last_launch());
     if (stop) break;
     R.restarts++;
@@ -342,6 +352,7 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
   // true residual
   HFMM_TRY(A(x, W.w));
   k_sub<<<gN, 256, 0, s>>>(b, W.w, W.r, N);
+  count_launches(1);
   HFMM_TRY(dev_norm(W, W.r, N, W.scal + 6, s));
   HFMM_CUDA_TRY(cudaMemcpyAsync(W.host, W.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
   HFMM_CUDA_TRY(cudaStreamSynchronize(s));

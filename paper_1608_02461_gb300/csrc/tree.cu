@@ -222,6 +222,98 @@ __global__ void k_m2l_slots(int box, const int* count, int* off, int* box_index,
   *nslots = ns;
 }
 
+// ---- M2L target tiles
+
+// cells of level 2 + blockIdx.x whose flags meet mask blockIdx.y + 1, one
+// thread per parity class b, in Morton order; region of class b at
+// level_off[l] + b 8^(l-1)
+__global__ void k_m2l_cells(const int* flags, const int64_t* level_off_dev, int* cells_all,
+                            int64_t cells_stride, int* counts) {
+  const int l = 2 + blockIdx.x;
+  const int mask = blockIdx.y + 1;
+  const int b = threadIdx.x;
+  if (b >= 8) return;
+  const int64_t off = level_off_dev[l];
+  const int per = 1 << (3 * (l - 1));
+  int* cells = cells_all + (mask - 1) * cells_stride + off + (int64_t)b * per;
+  int c = 0;
+  for (int j = 0; j < per; ++j) {
+    int cell = 8 * j + b;
+    if (flags[off + cell] & mask) cells[c++] = cell;
+  }
+  counts[((mask - 1) * (HFMM_MAX_LEVEL + 1) + l) * 8 + b] = c;
+}
+
+// one thread per mask: tiles of at most tc cells of one (level, class)
+__global__ void k_m2l_tiles(int L, int tc, const int64_t* level_off_dev, const int* counts,
+                            int4* tiles_all, int64_t tiles_stride, int* ntiles) {
+  const int mi = threadIdx.x;
+  if (mi >= 3) return;
+  int4* tiles = tiles_all + mi * tiles_stride;
+  int n = 0;
+  for (int l = 2; l <= L; ++l) {
+    const int per = 1 << (3 * (l - 1));
+    for (int b = 0; b < 8; ++b) {
+      int cnt = counts[(mi * (HFMM_MAX_LEVEL + 1) + l) * 8 + b];
+      int64_t base = level_off_dev[l] + (int64_t)b * per;
+      for (int st = 0; st < cnt; st += tc) tiles[n++] = make_int4(l, b, (int)(base + st), min(tc, cnt - st));
+    }
+  }
+  ntiles[mi] = n;
+}
+
+// ---- algorithmic work counts (statistics and roofline accounting)
+
+__global__ void k_count_m2l(int level, const int* flags, const int* m2l_off, int m2l_count,
+                            unsigned long long* cnt) {
+  __shared__ unsigned long long loc[16];
+  if (threadIdx.x < 16) loc[threadIdx.x] = 0;
+  __syncthreads();
+  int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = 1 << level;
+  if (cell < s * s * s) {
+    int ft = flags[cell];
+    int b = cell & 7;
+    int ix, iy, iz;
+    morton_decode((uint64_t)cell, ix, iy, iz);
+    unsigned long long c[4] = {0, 0, 0, 0};
+    for (int i = 0; i < m2l_count; ++i) {
+      int o = m2l_off[b * m2l_count + i];
+      int jx = ix + (o & 255) - 128, jy = iy + ((o >> 8) & 255) - 128, jz = iz + ((o >> 16) & 255) - 128;
+      if (jx < 0 || jy < 0 || jz < 0 || jx >= s || jy >= s || jz >= s) continue;
+      c[flags[morton_encode(jx, jy, jz)]]++;
+    }
+    for (int f = 0; f < 4; ++f)
+      if (c[f]) atomicAdd(&loc[ft * 4 + f], c[f]);
+  }
+  __syncthreads();
+  if (threadIdx.x < 16 && loc[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], loc[threadIdx.x]);
+}
+
+__global__ void k_count_p2p(int L, const int* leaf_start, const int* leaf_mid, const int* near_off,
+                            int near_count, unsigned long long* cnt) {
+  int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = 1 << L;
+  if (leaf >= s * s * s) return;
+  unsigned long long tv = leaf_mid[leaf] - leaf_start[leaf], tb = leaf_start[leaf + 1] - leaf_mid[leaf];
+  if (tv + tb == 0) return;
+  int ix, iy, iz;
+  morton_decode((uint64_t)leaf, ix, iy, iz);
+  unsigned long long sv = 0, sb = 0;
+  for (int i = 0; i < near_count; ++i) {
+    int o = near_off[i];
+    int jx = ix + (o & 255) - 128, jy = iy + ((o >> 8) & 255) - 128, jz = iz + ((o >> 16) & 255) - 128;
+    if (jx < 0 || jy < 0 || jz < 0 || jx >= s || jy >= s || jz >= s) continue;
+    int m = (int)morton_encode(jx, jy, jz);
+    sv += leaf_mid[m] - leaf_start[m];
+    sb += leaf_start[m + 1] - leaf_mid[m];
+  }
+  atomicAdd(&cnt[0], tv * sv);
+  atomicAdd(&cnt[1], tv * sb);
+  atomicAdd(&cnt[2], tb * sv);
+  atomicAdd(&cnt[3], tb * sb);
+}
+
 // ---- self terms
 
 // radial integrals along a ray of length R from the singular point:
@@ -456,5 +548,87 @@ int build_self_terms(fmm_tree* t, cudaStream_t s) {
   const double h3 = t->h * t->h * t->h, h2 = t->h * t->h;
   t->sigma_vol = make_double2(hs[0].x / h3, hs[0].y / h3);
   t->sigma_bnd = make_double2(hs[1].x / h2, hs[1].y / h2);
+  return HFMM_OK;
+}
+
+int build_pair_counts(fmm_tree* t, cudaStream_t s) {
+  unsigned long long* d = nullptr;
+  const int nc = (HFMM_MAX_LEVEL + 1) * 16 + 4;
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&d, sizeof(unsigned long long) * nc, s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long) * nc, s));
+  for (int l = 2; l <= t->L; ++l) {
+    int ncell = 1 << (3 * l);
+    k_count_m2l<<<ceil_div(ncell, 128), 128, 0, s>>>(l, t->flags + t->level_off[l], t->m2l_off,
+                                                      t->m2l_count, d + l * 16);
+  }
+  int nleaf = 1 << (3 * t->L);
+  k_count_p2p<<<ceil_div(nleaf, 128), 128, 0, s>>>(t->L, t->leaf_start, t->leaf_mid, t->near_off,
+                                                    t->near_count, d + (HFMM_MAX_LEVEL + 1) * 16);
+  HFMM_TRY(hfmm_last_launch());
+  std::vector<unsigned long long> h(nc);
+  HFMM_CUDA_TRY(cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * nc, cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFreeAsync(d, s);
+  for (int l = 0; l <= HFMM_MAX_LEVEL; ++l)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) t->m2l_cnt[l][a][b] = (int64_t)h[l * 16 + a * 4 + b];
+  for (int i = 0; i < 4; ++i) t->p2p_cnt[i] = (int64_t)h[(HFMM_MAX_LEVEL + 1) * 16 + i];
+  return HFMM_OK;
+}
+
+double p2p_work(const fmm_tree* t, int src_set, int tgt_set) {
+  double w = 0;
+  for (int ti = 0; ti < 2; ++ti)
+    for (int si = 0; si < 2; ++si)
+      if ((tgt_set & (1 << ti)) && (src_set & (1 << si))) w += (double)t->p2p_cnt[2 * ti + si];
+  // j != i: a point that is both source and target does not meet itself
+  if ((src_set & tgt_set) & HFMM_SET_VOL) w -= (double)t->n_vol;
+  if ((src_set & tgt_set) & HFMM_SET_BND) w -= (double)t->n_bnd;
+  return w;
+}
+
+double m2l_work(const fmm_tree* t, int src_set, int tgt_set) {
+  double pairs = 0;
+  for (int l = 2; l <= t->L; ++l)
+    for (int ft = 0; ft < 4; ++ft)
+      for (int fs = 0; fs < 4; ++fs)
+        if ((ft & tgt_set) && (fs & src_set)) pairs += (double)t->m2l_cnt[l][ft][fs];
+  return 8.0 * t->P * t->P * pairs;
+}
+
+int build_m2l_tiles(fmm_tree* t, cudaStream_t s) {
+  // tile width: 32 target cells (the offset lists are split over blocks when
+  // that gives too few tiles for the GPU)
+  int64_t cells_l = 0;
+  for (int l = 2; l <= t->L; ++l) cells_l += (int64_t)1 << (3 * l);
+  t->m2l_tc = 32;
+  const int64_t cstride = t->total_cells;
+  const int64_t tstride = cells_l / t->m2l_tc + 8 * (t->L + 1) + 8;
+  int* cells = nullptr;
+  int4* tiles = nullptr;
+  HFMM_TRY(tree_alloc_t(t, &cells, 3 * cstride));
+  HFMM_TRY(tree_alloc_t(t, &tiles, 3 * tstride));
+  int* d_counts = nullptr;
+  int64_t* d_off = nullptr;
+  const int ncount = 3 * (HFMM_MAX_LEVEL + 1) * 8 + 4;
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&d_counts, sizeof(int) * ncount, s));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&d_off, sizeof(t->level_off), s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(d_counts, 0, sizeof(int) * ncount, s));
+  HFMM_CUDA_TRY(cudaMemcpyAsync(d_off, t->level_off, sizeof(t->level_off), cudaMemcpyHostToDevice, s));
+  k_m2l_cells<<<dim3(t->L - 1, 3), 32, 0, s>>>(t->flags, d_off, cells, cstride, d_counts);
+  k_m2l_tiles<<<1, 32, 0, s>>>(t->L, t->m2l_tc, d_off, d_counts, tiles, tstride,
+                               d_counts + 3 * (HFMM_MAX_LEVEL + 1) * 8);
+  HFMM_TRY(hfmm_last_launch());
+  int nt[3];
+  HFMM_CUDA_TRY(cudaMemcpyAsync(nt, d_counts + 3 * (HFMM_MAX_LEVEL + 1) * 8, sizeof(nt),
+                                cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFreeAsync(d_counts, s);
+  cudaFreeAsync(d_off, s);
+  for (int i = 0; i < 3; ++i) {
+    t->m2l_cells[i] = cells + i * cstride;
+    t->m2l_tiles[i] = tiles + i * tstride;
+    t->m2l_ntiles[i] = nt[i];
+  }
   return HFMM_OK;
 }

@@ -14,6 +14,67 @@ struct DevBuf {
 
 struct fmm_tree_ext;  // solver workspaces (capi.cu)
 
+// kernels launched by the library (all handles)
+void count_launches(int64_t n);
+int64_t launches_so_far();
+
+// Per-stage CUDA-event timing: pairs of events recorded around each stage's
+// launches, resolved lazily (flush) so that timing adds no synchronisation.
+struct StageTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> stage_of;  // per recorded pair
+  size_t used = 0;            // events used in the pool
+  double ms[HFMM_NSTAGES] = {0};
+  int64_t launches[HFMM_NSTAGES] = {0};
+  double work[HFMM_NSTAGES] = {0};
+  void begin(int stage, cudaStream_t s) {
+    if (!on) return;
+    if (used + 2 > pool.size()) {
+      if (pool.size() >= 8192) flush();
+      while (used + 2 > pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        pool.push_back(e);
+      }
+    }
+    cudaEventRecord(pool[used], s);
+    stage_of.push_back(stage);
+  }
+  void end(int nlaunch, cudaStream_t s, double w = 0.0) {
+    if (!on) return;
+    cudaEventRecord(pool[used + 1], s);
+    launches[stage_of.back()] += nlaunch;
+    work[stage_of.back()] += w;
+    used += 2;
+  }
+  void flush() {
+    if (used == 0) return;
+    cudaEventSynchronize(pool[used - 1]);
+    for (size_t i = 0; i < stage_of.size(); ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) ms[stage_of[i]] += t;
+    }
+    cudaGetLastError();
+    stage_of.clear();
+    used = 0;
+  }
+  void reset() {
+    flush();
+    for (int i = 0; i < HFMM_NSTAGES; ++i) {
+      ms[i] = 0;
+      launches[i] = 0;
+      work[i] = 0;
+    }
+  }
+  void destroy() {
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+    stage_of.clear();
+    used = 0;
+  }
+};
+
 struct fmm_tree {
   fmm_tree_ext* ext = nullptr;
   // ---- problem
@@ -39,6 +100,7 @@ struct fmm_tree {
   int* leaf_mid = nullptr;      // [8^L] first boundary point of each leaf
   int* flags = nullptr;         // per level, per Morton cell: bit0 volume points, bit1 boundary
   int64_t level_off[HFMM_MAX_LEVEL + 2] = {0};  // first cell of level l in the per-cell arrays
+  int64_t* level_off_dev = nullptr;             // device copy
   int64_t total_cells = 0;
 
   // ---- interaction lists (offsets in cell units)
@@ -49,6 +111,14 @@ struct fmm_tree {
   int* m2l_off = nullptr;       // [8][m2l_count] packed offsets
   int* m2l_box_index = nullptr; // [8][m2l_count] operator slot of each list entry
   int* m2l_slot_off = nullptr;  // [slots] packed offset of each operator slot
+  // target cells of the M2L, per target-set mask (index mask - 1), grouped by
+  // level and parity class, and tiles {level, class, first, count} over them
+  int m2l_tc = 32;              // target cells per tile
+  int* m2l_cells[3] = {nullptr, nullptr, nullptr};
+  int4* m2l_tiles[3] = {nullptr, nullptr, nullptr};
+  int m2l_ntiles[3] = {0, 0, 0};
+  void* m2l_part = nullptr;     // [m2l_part_max][total_cells][P] split-offset partial sums
+  int m2l_part_max = 1;
 
   // ---- operators (FP64 master copy; FP32 copy for the FP32 form)
   double2* op_m2m = nullptr;    // [L+1][8][P][P]   row a' (out), column a (in)
@@ -76,8 +146,13 @@ struct fmm_tree {
 
   // ---- counters
   int64_t m2l_pairs = 0, p2p_pairs = 0;
+  // cell pairs per level by (target flags, source flags), and near-field
+  // point pairs by (target set, source set) with index 2*(tgt==BND)+(src==BND)
+  int64_t m2l_cnt[HFMM_MAX_LEVEL + 1][4][4] = {};
+  int64_t p2p_cnt[4] = {0, 0, 0, 0};
   double ms_last_apply = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  StageTimer timer;
 
   std::vector<DevBuf> bufs;
   int64_t device_bytes = 0;
@@ -94,6 +169,10 @@ inline int tree_alloc_t(fmm_tree* t, X** ptr, size_t count) {
 int build_geometry_and_sort(fmm_tree* t, const double* d_vol, const double* d_bnd, cudaStream_t s);
 int build_lists(fmm_tree* t, cudaStream_t s);
 int build_self_terms(fmm_tree* t, cudaStream_t s);
+int build_pair_counts(fmm_tree* t, cudaStream_t s);
+int build_m2l_tiles(fmm_tree* t, cudaStream_t s);
+double p2p_work(const fmm_tree* t, int src_set, int tgt_set);
+double m2l_work(const fmm_tree* t, int src_set, int tgt_set);
 
 // operators.cu
 int build_operators(fmm_tree* t, cudaStream_t s);
@@ -102,6 +181,8 @@ int build_operators(fmm_tree* t, cudaStream_t s);
 int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol,
                const double2* q_bnd, double scale_bnd, cudaStream_t s);
 int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
+// HFMM_ERR_TIMEOUT (or 0) recorded by a kernel's bounded wait; synchronises s
+int fmm_device_error(cudaStream_t s, bool clear);
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cudaStream_t s);
 
 // krylov.cu

@@ -47,11 +47,18 @@ class hfmm_gmres_info(ctypes.Structure):
                 ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int)]
 
 
+NSTAGES = 8
+STAGES = ["gather", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "fdm"]
+
+
 class hfmm_stats(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("p", ctypes.c_int), ("n_vol", ctypes.c_int64),
                 ("n_bnd", ctypes.c_int64), ("leaves", ctypes.c_int64),
                 ("m2l_pairs", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("ms_last_apply", ctypes.c_double)]
+                ("device_bytes", ctypes.c_int64), ("ms_last_apply", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("stage_ms", ctypes.c_double * NSTAGES),
+                ("stage_launches", ctypes.c_int64 * NSTAGES),
+                ("stage_work", ctypes.c_double * NSTAGES)]
 
 
 # name -> (restype, argtypes) for every entry point of include/hfmm.h
@@ -73,6 +80,7 @@ SIGNATURES = {
                                    ctypes.POINTER(hfmm_gmres_params),
                                    ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
     "fmm_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hfmm_stats)]),
+    "fmm_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
 }
 
 _lib = None
@@ -225,6 +233,16 @@ class Tree:
         gi = GmresInfo(info.iters, info.restarts, info.inner_iters_total, info.status,
                        info.relres_est, info.relres_true, list(hist[:min(info.iters, history_len)]))
         return x, gi
+
+    def set_timing(self, on: bool):
+        _check(lib().fmm_set_timing(self._h, 1 if on else 0), "fmm_set_timing")
+
+    def stage_times(self):
+        """{stage: (ms, launches, work)} accumulated since set_timing(True);
+        work is point pairs for p2p and flops for m2l."""
+        s = self.stats()
+        return {name: (s.stage_ms[i], s.stage_launches[i], s.stage_work[i])
+                for i, name in enumerate(STAGES)}
 
     def stats(self) -> hfmm_stats:
         s = hfmm_stats()
