@@ -2,6 +2,7 @@
 // the FMM apply, the BEM-coupled preconditioner (Sec. 5.2-5.3) and the outer
 // preconditioned GMRES (Sec. 3-4, Sec. 6).
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <atomic>
 #include <new>
@@ -103,7 +104,13 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   HFMM_TRY(tree_alloc(t, &t->Lc, csz * t->total_cells * P));
   HFMM_TRY(tree_alloc(t, &t->qs, csz * N));
   HFMM_TRY(tree_alloc(t, &t->phis, csz * N));
+  HFMM_TRY(tree_alloc(t, &t->zero_row, csz * (P + 2)));
+  HFMM_CUDA_TRY(cudaMemsetAsync(t->zero_row, 0, csz * (P + 2), s));
   t->m2l_part_max = 8;
+  // M2L pipeline: the warp-specialised form wins once the operator is large
+  // (p >= 8), the block-synchronous two-stage form below that (measured)
+  t->m2l_variant = P >= 64 ? 1 : 0;
+  if (const char* v = getenv("HFMM_M2L_VARIANT")) t->m2l_variant = atoi(v);
   HFMM_TRY(tree_alloc(t, &t->m2l_part, csz * t->total_cells * P * t->m2l_part_max));
   HFMM_TRY(tree_alloc_t(t, &t->g_bnd, t->n_bnd + 1));
   HFMM_TRY(tree_alloc_t(t, &t->q_bnd, t->n_bnd + 1));

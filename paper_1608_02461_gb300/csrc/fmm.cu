@@ -217,7 +217,11 @@ __global__ void k_m2l(FmmDev<T> d, int level, int64_t off, const C<T>* ops, cons
     const C<T>* Top = ops + (int64_t)m2l_slot[b * m2l_count + i] * P * P;
     for (int q = 0; q < 4; ++q) {
       int ap = threadIdx.x + q * blockDim.x;
-      if (ap < P) acc[q] = cadd<T>(acc[q], matvec_row<T>(Top, ap, xs, P));
+      if (ap < P) {  // row-major operator: row ap is contiguous
+        C<T> v = mkc<T>(0, 0);
+        for (int a = 0; a < P; ++a) cfma<T>(v, Top[(int64_t)ap * P + a], xs[a]);
+        acc[q] = cadd<T>(acc[q], v);
+      }
     }
   }
   for (int q = 0; q < 4; ++q) {
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(128) k_m2l_tiled(FmmDev<T> d, const int4* __re
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         int ap = r0 + r * RT;
-        tv[r] = ap < P ? Ts[a * P + ap] : mkc<T>(0, 0);
+        tv[r] = ap < P ? Ts[ap * P + a] : mkc<T>(0, 0);
       }
 #pragma unroll
       for (int j = 0; j < CM; ++j) mv[j] = Ms[a * (TC + 1) + c0 + j * CT];
@@ -376,35 +380,141 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-template <typename T, int R, int CM>
-__global__ void __launch_bounds__(128) k_m2l_tma(FmmDev<T> d, const int4* __restrict__ tiles,
-                                                 const int* __restrict__ cells,
-                                                 const int64_t* __restrict__ level_off,
-                                                 const C<T>* __restrict__ ops, int64_t box_cells,
-                                                 const int* __restrict__ m2l_off,
-                                                 const int* __restrict__ m2l_slot, int m2l_count,
-                                                 int src_set, C<T>* __restrict__ part, int64_t part_stride) {
-  constexpr int CT = 8, RT = 16, TC = CT * CM;
-  const int P = d.P;
-  const int MS = P + 2;  // padded source row (16-byte multiple, spreads banks)
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);                  // [2]
-  int* vlist = reinterpret_cast<int*>(smem_raw + 16);                     // [m2l_count] valid offsets
-  unsigned* vmask = reinterpret_cast<unsigned*>(vlist + m2l_count);       // [m2l_count] column masks
-  int* tcell = reinterpret_cast<int*>(vmask + m2l_count);                 // [TC]
-  int* tco = tcell + TC;                                                  // [TC][3]
-  int* nval = tco + 3 * TC;                                               // [1]
-  size_t hdr = 16 + sizeof(int) * (2 * (size_t)m2l_count + 4 * TC + 4);
-  hdr = (hdr + 127) & ~(size_t)127;
-  C<T>* Ts = reinterpret_cast<C<T>*>(smem_raw + hdr);                    // [2][P*P]
-  C<T>* Ms = Ts + 2 * (size_t)P * P;                                      // [2][TC][MS]
-
+// Valid offsets of every tile for one source-set mask: the offsets (in list
+// order) for which at least one tile cell has a source cell holding points of
+// the set, with the mask of those columns.  One block per tile, one-time.
+__global__ void k_m2l_valid(const int4* __restrict__ tiles, const int* __restrict__ cells,
+                            const int* __restrict__ flags, const int64_t* __restrict__ level_off,
+                            const int* __restrict__ m2l_off, int m2l_count, int src_set,
+                            int* __restrict__ vlist, unsigned* __restrict__ vmask, int* __restrict__ nval) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned* msk = reinterpret_cast<unsigned*>(smem_raw);  // [m2l_count]
+  __shared__ int tco[32][3];
+  __shared__ int tval[32];
   const int4 tile = tiles[blockIdx.x];
   const int level = tile.x, b = tile.y, first = tile.z, cnt = tile.w;
   const int64_t off = level_off[level];
   const int s = 1 << level;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  if (tid < 32) {
+    int cell = tid < cnt ? cells[first + tid] : -1;
+    int ix = 0, iy = 0, iz = 0;
+    if (cell >= 0) morton_decode((uint64_t)cell, ix, iy, iz);
+    tco[tid][0] = ix;
+    tco[tid][1] = iy;
+    tco[tid][2] = iz;
+    tval[tid] = cell >= 0;
+  }
+  __syncthreads();
+  for (int i = warp; i < m2l_count; i += nw) {
+    const int o = m2l_off[b * m2l_count + i];
+    bool v = false;
+    if (tval[lane]) {
+      int jx = tco[lane][0] + (o & 255) - 128, jy = tco[lane][1] + ((o >> 8) & 255) - 128,
+          jz = tco[lane][2] + ((o >> 16) & 255) - 128;
+      if (jx >= 0 && jy >= 0 && jz >= 0 && jx < s && jy < s && jz < s)
+        v = (flags[off + morton_encode(jx, jy, jz)] & src_set) != 0;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, v);
+    if (lane == 0) msk[i] = m;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0;
+    int* vl = vlist + (int64_t)blockIdx.x * m2l_count;
+    unsigned* vm = vmask + (int64_t)blockIdx.x * m2l_count;
+    for (int i = 0; i < m2l_count; ++i)
+      if (msk[i]) {
+        vl[n] = i;
+        vm[n] = msk[i];
+        ++n;
+      }
+    nval[blockIdx.x] = n;
+  }
+}
+
+// RT row groups x 8 column groups of threads; a thread owns rows r0 + r RT
+// (r < R) and columns c0 + j 8 (j < CM) of the P x TC output tile.
+// acc[r][j] += sum_a T(r0 + r RT, a) M(c0 + 8 j, a) for one staged offset:
+// T row-major (P x P), source rows of stride MS; two consecutive a per step
+// read with one 16-byte load per row (FP32) or two (FP64).  P is even.
+template <typename T, int R, int CM, int RT>
+__device__ __forceinline__ void m2l_block_product(const C<T>* __restrict__ Ts, const C<T>* __restrict__ Ms,
+                                                  int P, int MS, int r0, int c0, C<T> (&acc)[R][CM]) {
+  constexpr int CT = 8;
+  const C<T>* trow[R];
+  const C<T>* mrow[CM];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int ap = r0 + r * RT;
+    trow[r] = Ts + (size_t)(ap < P ? ap : 0) * P;
+  }
+#pragma unroll
+  for (int j = 0; j < CM; ++j) mrow[j] = Ms + (size_t)(c0 + j * CT) * MS;
+#pragma unroll 2
+  for (int a = 0; a < P; a += 2) {
+    C<T> t0[R], t1[R], m0[CM], m1[CM];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if constexpr (sizeof(T) == 4) {
+        float4 v = *reinterpret_cast<const float4*>(trow[r] + a);
+        t0[r] = mkc<T>(v.x, v.y);
+        t1[r] = mkc<T>(v.z, v.w);
+      } else {
+        t0[r] = trow[r][a];
+        t1[r] = trow[r][a + 1];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CM; ++j) {
+      if constexpr (sizeof(T) == 4) {
+        float4 v = *reinterpret_cast<const float4*>(mrow[j] + a);
+        m0[j] = mkc<T>(v.x, v.y);
+        m1[j] = mkc<T>(v.z, v.w);
+      } else {
+        m0[j] = mrow[j][a];
+        m1[j] = mrow[j][a + 1];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int j = 0; j < CM; ++j) {
+        cfma<T>(acc[r][j], t0[r], m0[j]);
+        cfma<T>(acc[r][j], t1[r], m1[j]);
+      }
+  }
+}
+
+template <typename T, int R, int CM, int RT>
+__global__ void __launch_bounds__(RT * 8) k_m2l_tma(FmmDev<T> d, const int4* __restrict__ tiles,
+                                                    const int* __restrict__ cells,
+                                                    const int64_t* __restrict__ level_off,
+                                                    const C<T>* __restrict__ ops, int64_t box_cells,
+                                                    const int* __restrict__ m2l_off,
+                                                    const int* __restrict__ m2l_slot, int m2l_count,
+                                                    const int* __restrict__ vlist_all,
+                                                    const unsigned* __restrict__ vmask_all,
+                                                    const int* __restrict__ nval_all,
+                                                    const C<T>* __restrict__ zero_row,
+                                                    C<T>* __restrict__ part, int64_t part_stride) {
+  constexpr int CT = 8, TC = CT * CM, NT = RT * CT;
+  const int P = d.P;
+  const int MS = P + 2;  // padded source row (16-byte multiple, spreads banks)
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [2]
+  int* tcell = reinterpret_cast<int*>(smem_raw + 16);      // [TC]
+  int* tco = tcell + TC;                                   // [TC][3]
+  C<T>* Ts = reinterpret_cast<C<T>*>(smem_raw + 1024);     // [2][P*P]
+  C<T>* Ms = Ts + 2 * (size_t)P * P;                       // [2][TC][MS]
+
+  const int4 tile = tiles[blockIdx.x];
+  const int level = tile.x, b = tile.y, first = tile.z, cnt = tile.w;
+  const int64_t off = level_off[level];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = tid / CT, c0 = tid % CT;
+  const int* vlist = vlist_all + (int64_t)blockIdx.x * m2l_count;
+  const unsigned* vmask = vmask_all + (int64_t)blockIdx.x * m2l_count;
   if (tid < TC) {
     int cell = tid < cnt ? cells[first + tid] : -1;
     tcell[tid] = cell;
@@ -420,57 +530,37 @@ __global__ void __launch_bounds__(128) k_m2l_tma(FmmDev<T> d, const int4* __rest
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // valid offsets and their column masks (one warp per offset, lane = column)
-  for (int i = warp; i < m2l_count; i += 4) {
-    const int o = m2l_off[b * m2l_count + i];
-    bool v = false;
-    if (lane < TC && tcell[lane] >= 0) {
-      int jx = tco[3 * lane] + (o & 255) - 128, jy = tco[3 * lane + 1] + ((o >> 8) & 255) - 128,
-          jz = tco[3 * lane + 2] + ((o >> 16) & 255) - 128;
-      if (jx >= 0 && jy >= 0 && jz >= 0 && jx < s && jy < s && jz < s)
-        v = (d.flags[off + morton_encode(jx, jy, jz)] & src_set) != 0;
-    }
-    unsigned m = __ballot_sync(0xffffffffu, v);
-    if (lane == 0) vmask[i] = m;
-  }
-  __syncthreads();
-  if (tid == 0) {  // compact in offset order
-    int n = 0;
-    for (int i = 0; i < m2l_count; ++i)
-      if (vmask[i]) {
-        vmask[n] = vmask[i];
-        vlist[n++] = i;
-      }
-    *nval = n;
-  }
-  __syncthreads();
-  const int nv = *nval;
-  // this block's share of the valid offsets
+  const int nv = nval_all[blockIdx.x];
   const int ks = blockIdx.y, kn = gridDim.y;
   const int sbeg = (int)((int64_t)nv * ks / kn), send = (int)((int64_t)nv * (ks + 1) / kn);
   const C<T>* opsl = ops + (int64_t)level * box_cells * P * P;
   const uint32_t op_bytes = (uint32_t)((size_t)P * P * sizeof(C<T>));
   const uint32_t row_bytes = (uint32_t)((size_t)P * sizeof(C<T>));
 
-  // warp 0 issues the copies of step `st` into stage (st - sbeg) & 1
+  // warp 0 issues the copies of step `st` into stage (st - sbeg) & 1: the
+  // operator, and for each of the TC columns either its source row or a row
+  // of zeros (so that the product needs no masking)
   auto issue = [&](int st) {
     const int i = vlist[st];
     const unsigned m = vmask[st];
     const int stg = (st - sbeg) & 1;
     if (lane == 0) {
       fence_async_shared();
-      mbar_expect_tx(&bar[stg], op_bytes + (uint32_t)__popc(m) * row_bytes);
+      mbar_expect_tx(&bar[stg], op_bytes + (uint32_t)TC * row_bytes);
     }
     __syncwarp();
     if (lane == 0)
       bulk_copy_g2s(Ts + (size_t)stg * P * P, opsl + (int64_t)m2l_slot[b * m2l_count + i] * P * P, op_bytes,
                     &bar[stg]);
-    if (lane < TC && (m >> lane) & 1u) {
-      const int o = m2l_off[b * m2l_count + i];
-      int jx = tco[3 * lane] + (o & 255) - 128, jy = tco[3 * lane + 1] + ((o >> 8) & 255) - 128,
-          jz = tco[3 * lane + 2] + ((o >> 16) & 255) - 128;
-      int64_t src = (int64_t)morton_encode(jx, jy, jz);
-      bulk_copy_g2s(Ms + ((size_t)stg * TC + lane) * MS, d.M + (off + src) * P, row_bytes, &bar[stg]);
+    if (lane < TC) {
+      const C<T>* src = zero_row;
+      if ((m >> lane) & 1u) {
+        const int o = m2l_off[b * m2l_count + i];
+        int jx = tco[3 * lane] + (o & 255) - 128, jy = tco[3 * lane + 1] + ((o >> 8) & 255) - 128,
+            jz = tco[3 * lane + 2] + ((o >> 16) & 255) - 128;
+        src = d.M + (off + (int64_t)morton_encode(jx, jy, jz)) * P;
+      }
+      bulk_copy_g2s(Ms + ((size_t)stg * TC + lane) * MS, src, row_bytes, &bar[stg]);
     }
   };
 
@@ -491,29 +581,7 @@ __global__ void __launch_bounds__(128) k_m2l_tma(FmmDev<T> d, const int4* __rest
       failed_at = st;
       break;
     }
-    const unsigned m = vmask[st];
-    bool cv[CM];
-#pragma unroll
-    for (int j = 0; j < CM; ++j) cv[j] = (m >> (c0 + j * CT)) & 1u;
-    const C<T>* Tst = Ts + (size_t)stg * P * P;
-    const C<T>* Mst = Ms + (size_t)stg * TC * MS;
-    for (int a = 0; a < P; ++a) {
-      C<T> tv[R], mv[CM];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        int ap = r0 + r * RT;
-        tv[r] = ap < P ? Tst[a * P + ap] : mkc<T>(0, 0);
-      }
-#pragma unroll
-      for (int j = 0; j < CM; ++j) {
-        C<T> v = Mst[(c0 + j * CT) * MS + a];
-        mv[j] = cv[j] ? v : mkc<T>(0, 0);
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int j = 0; j < CM; ++j) cfma<T>(acc[r][j], tv[r], mv[j]);
-    }
+    m2l_block_product<T, R, CM, RT>(Ts + (size_t)stg * P * P, Ms + (size_t)stg * TC * MS, P, MS, r0, c0, acc);
     __syncthreads();  // stage free for the copy issued in the next step
   }
   if (failed_at >= 0) {
@@ -541,6 +609,160 @@ __global__ void __launch_bounds__(128) k_m2l_tma(FmmDev<T> d, const int4* __rest
           d.Lc[(off + tcell[c]) * P + ap] = acc[r][j];
       }
     }
+  (void)NT;
+}
+
+// Warp-specialised form of k_m2l_tma: one producer warp streams the
+// operator and source rows of each valid offset through NSTG shared-memory
+// stages with bulk copies (full barrier per stage, completed by the copies'
+// byte count), and RT * 8 consumer threads multiply; consumers release a
+// stage through its empty barrier (one arrival per consumer warp), so no
+// block-wide barrier sits in the main loop.  Every wait is bounded; a wait
+// that gives up raises a block-wide abort flag, records HFMM_ERR_TIMEOUT and
+// the block leaves without writing results.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (global_ns() - t0 < 1000000000ull) {
+    if (*abort_flag) return false;
+    if (mbar_try_wait(bar, parity)) return true;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+template <typename T, int R, int CM, int RT, int NSTG>
+__global__ void __launch_bounds__(RT * 8 + 32) k_m2l_ws(FmmDev<T> d, const int4* __restrict__ tiles,
+                                                        const int* __restrict__ cells,
+                                                        const int64_t* __restrict__ level_off,
+                                                        const C<T>* __restrict__ ops, int64_t box_cells,
+                                                        const int* __restrict__ m2l_off,
+                                                        const int* __restrict__ m2l_slot, int m2l_count,
+                                                        const int* __restrict__ vlist_all,
+                                                        const unsigned* __restrict__ vmask_all,
+                                                        const int* __restrict__ nval_all,
+                                                        const C<T>* __restrict__ zero_row,
+                                                        C<T>* __restrict__ part, int64_t part_stride) {
+  constexpr int CT = 8, TC = CT * CM, NC = RT * CT, NCW = NC / 32;
+  const int P = d.P;
+  const int MS = P + 2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);           // [NSTG]
+  uint64_t* empty = full + NSTG;                                     // [NSTG]
+  int* abort_flag = reinterpret_cast<int*>(empty + NSTG);
+  int* tcell = abort_flag + 4;                                       // [TC]
+  int* tco = tcell + TC;                                             // [TC][3]
+  C<T>* Ts = reinterpret_cast<C<T>*>(smem_raw + 1024);              // [NSTG][P*P]
+  C<T>* Ms = Ts + NSTG * (size_t)P * P;                              // [NSTG][TC][MS]
+
+  const int4 tile = tiles[blockIdx.x];
+  const int level = tile.x, b = tile.y, first = tile.z, cnt = tile.w;
+  const int64_t off = level_off[level];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int* vlist = vlist_all + (int64_t)blockIdx.x * m2l_count;
+  const unsigned* vmask = vmask_all + (int64_t)blockIdx.x * m2l_count;
+  if (tid < TC) {
+    int cell = tid < cnt ? cells[first + tid] : -1;
+    tcell[tid] = cell;
+    int ix = 0, iy = 0, iz = 0;
+    if (cell >= 0) morton_decode((uint64_t)cell, ix, iy, iz);
+    tco[3 * tid] = ix;
+    tco[3 * tid + 1] = iy;
+    tco[3 * tid + 2] = iz;
+  }
+  if (tid == 0) {
+    for (int q = 0; q < NSTG; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], NCW);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int nv = nval_all[blockIdx.x];
+  const int ks = blockIdx.y, kn = gridDim.y;
+  const int sbeg = (int)((int64_t)nv * ks / kn), send = (int)((int64_t)nv * (ks + 1) / kn);
+  const int nsteps = send - sbeg;
+  volatile int* abf = abort_flag;
+
+  if (warp == NCW) {
+    // ---------------- producer warp
+    const C<T>* opsl = ops + (int64_t)level * box_cells * P * P;
+    const uint32_t op_bytes = (uint32_t)((size_t)P * P * sizeof(C<T>));
+    const uint32_t row_bytes = (uint32_t)((size_t)P * sizeof(C<T>));
+    for (int kk = 0; kk < nsteps; ++kk) {
+      const int stg = kk % NSTG;
+      bool ok = true;
+      if (kk >= NSTG) ok = mbar_wait_abortable(&empty[stg], (uint32_t)(((kk / NSTG) - 1) & 1), abf);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      const int st = sbeg + kk;
+      const int i = vlist[st];
+      const unsigned m = vmask[st];
+      if (lane == 0) {
+        fence_async_shared();
+        mbar_expect_tx(&full[stg], op_bytes + (uint32_t)TC * row_bytes);
+      }
+      __syncwarp();
+      if (lane == 0)
+        bulk_copy_g2s(Ts + (size_t)stg * P * P, opsl + (int64_t)m2l_slot[b * m2l_count + i] * P * P,
+                      op_bytes, &full[stg]);
+      if (lane < TC) {
+        const C<T>* src = zero_row;
+        if ((m >> lane) & 1u) {
+          const int o = m2l_off[b * m2l_count + i];
+          int jx = tco[3 * lane] + (o & 255) - 128, jy = tco[3 * lane + 1] + ((o >> 8) & 255) - 128,
+              jz = tco[3 * lane + 2] + ((o >> 16) & 255) - 128;
+          src = d.M + (off + (int64_t)morton_encode(jx, jy, jz)) * P;
+        }
+        bulk_copy_g2s(Ms + ((size_t)stg * TC + lane) * MS, src, row_bytes, &full[stg]);
+      }
+    }
+    // wait for the copies of the last stages to land before leaving
+    for (int kk = (nsteps > NSTG ? nsteps - NSTG : 0); kk < nsteps; ++kk)
+      if (lane == 0) mbar_wait_abortable(&full[kk % NSTG], (uint32_t)((kk / NSTG) & 1), abf);
+    __syncwarp();
+  } else {
+    // ---------------- consumer warps
+    const int r0 = tid / CT, c0 = tid % CT;
+    C<T> acc[R][CM];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int j = 0; j < CM; ++j) acc[r][j] = mkc<T>(0, 0);
+    bool ok = true;
+    for (int kk = 0; kk < nsteps; ++kk) {
+      const int stg = kk % NSTG;
+      ok = mbar_wait_abortable(&full[stg], (uint32_t)((kk / NSTG) & 1), abf);
+      if (!__all_sync(0xffffffffu, ok)) {
+        ok = false;
+        break;
+      }
+      m2l_block_product<T, R, CM, RT>(Ts + (size_t)stg * P * P, Ms + (size_t)stg * TC * MS, P, MS, r0, c0,
+                                      acc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stg]);
+    }
+    if (ok && !*abf) {
+      C<T>* out = part ? part + (int64_t)ks * part_stride : nullptr;
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < CM; ++j) {
+          int ap = r0 + r * RT, c = c0 + j * CT;
+          if (ap < P && c < cnt) {
+            if (out)
+              out[(int64_t)(first + c) * P + ap] = acc[r][j];
+            else
+              d.Lc[(off + tcell[c]) * P + ap] = acc[r][j];
+          }
+        }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && *abf) atomicExch(&g_fmm_error, HFMM_ERR_TIMEOUT);
 }
 
 // L of every tile cell = sum over the split parts, in part order
@@ -560,43 +782,71 @@ __global__ void k_m2l_reduce(FmmDev<T> d, const int4* __restrict__ tiles, const 
   }
 }
 
-template <typename T, int CM>
-int launch_m2l_tma(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
-                   cudaStream_t s) {
+// valid-offset lists of the tiles of target mask tm for source mask sm,
+// built on first use and kept by the handle
+int m2l_valid_lists(fmm_tree* t, int sm, int tm, cudaStream_t s) {
+  const int ci = (tm - 1) * 3 + (sm - 1);
+  if (t->m2l_vlist[ci]) return HFMM_OK;
+  const int nt = t->m2l_ntiles[tm - 1];
+  HFMM_TRY(tree_alloc_t(t, &t->m2l_vlist[ci], (size_t)nt * t->m2l_count + 1));
+  HFMM_TRY(tree_alloc_t(t, &t->m2l_vmask[ci], (size_t)nt * t->m2l_count + 1));
+  HFMM_TRY(tree_alloc_t(t, &t->m2l_nval[ci], (size_t)nt + 1));
+  if (nt == 0) return HFMM_OK;
+  k_m2l_valid<<<nt, 128, sizeof(unsigned) * t->m2l_count, s>>>(
+      t->m2l_tiles[tm - 1], t->m2l_cells[tm - 1], t->flags, t->level_off_dev, t->m2l_off, t->m2l_count,
+      sm, t->m2l_vlist[ci], t->m2l_vmask[ci], t->m2l_nval[ci]);
+  count_launches(1);
+  return hfmm_last_launch();
+}
+
+template <typename T, int CM, int R, int RT>
+int launch_m2l_tma_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
+                      cudaStream_t s) {
   const int P = t->P, mi = tgt_set - 1;
   const int TC = 8 * CM;
   const int nt = t->m2l_ntiles[mi];
   if (nt == 0) return HFMM_OK;
-  size_t hdr = 16 + sizeof(int) * (2 * (size_t)t->m2l_count + 4 * TC + 4);
-  hdr = (hdr + 127) & ~(size_t)127;
-  size_t sm = hdr + (2 * (size_t)P * P + 2 * (size_t)TC * (P + 2)) * sizeof(C<T>);
+  HFMM_TRY(m2l_valid_lists(t, src_set, tgt_set, s));
+  const int ci = mi * 3 + (src_set - 1);
+  size_t sm = 1024 + (2 * (size_t)P * P + 2 * (size_t)TC * (P + 2)) * sizeof(C<T>);
   // split the offset lists so that the grid fills the GPU a few times over
   int nsplit = (4 * 152 + nt - 1) / nt;
   if (nsplit > t->m2l_part_max) nsplit = t->m2l_part_max;
   if (nsplit < 1) nsplit = 1;
   C<T>* part = nsplit > 1 ? reinterpret_cast<C<T>*>(t->m2l_part) : nullptr;
   const int64_t pstride = t->total_cells * (int64_t)P;
-  const int R = (P + 15) / 16;
-  dim3 grid(nt, nsplit);
-#define HFMM_M2L_TMA_CASE(RR)                                                               \
-  if (R <= RR) {                                                                            \
-    HFMM_TRY(set_smem<T>((const void*)k_m2l_tma<T, RR, CM>, sm));                           \
-    k_m2l_tma<T, RR, CM><<<grid, 128, sm, s>>>(d, t->m2l_tiles[mi], t->m2l_cells[mi],       \
-                                               t->level_off_dev, ops, t->box_cells,         \
-                                               t->m2l_off, t->m2l_box_index, t->m2l_count,  \
-                                               src_set, part, pstride);                     \
-    if (nsplit > 1)                                                                         \
-      k_m2l_reduce<T><<<nt, 128, 0, s>>>(d, t->m2l_tiles[mi], t->m2l_cells[mi],             \
-                                         t->level_off_dev, part, pstride, nsplit);          \
-    count_launches(nsplit > 1 ? 2 : 1);                                                     \
-    return hfmm_last_launch();                                                              \
+  constexpr int NSTG = 3;
+  size_t smw = 1024 + (NSTG * (size_t)P * P + NSTG * (size_t)TC * (P + 2)) * sizeof(C<T>);
+  if (t->m2l_variant == 1 && smw <= 200 * 1024 && (RT * 8) % 32 == 0) {
+    HFMM_TRY(set_smem<T>((const void*)k_m2l_ws<T, R, CM, RT, NSTG>, smw));
+    k_m2l_ws<T, R, CM, RT, NSTG><<<dim3(nt, nsplit), RT * 8 + 32, smw, s>>>(
+        d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev, ops, t->box_cells, t->m2l_off,
+        t->m2l_box_index, t->m2l_count, t->m2l_vlist[ci], t->m2l_vmask[ci], t->m2l_nval[ci],
+        reinterpret_cast<const C<T>*>(t->zero_row), part, pstride);
+  } else {
+    HFMM_TRY(set_smem<T>((const void*)k_m2l_tma<T, R, CM, RT>, sm));
+    k_m2l_tma<T, R, CM, RT><<<dim3(nt, nsplit), RT * 8, sm, s>>>(
+        d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev, ops, t->box_cells, t->m2l_off,
+        t->m2l_box_index, t->m2l_count, t->m2l_vlist[ci], t->m2l_vmask[ci], t->m2l_nval[ci],
+        reinterpret_cast<const C<T>*>(t->zero_row), part, pstride);
   }
-  HFMM_M2L_TMA_CASE(1)
-  HFMM_M2L_TMA_CASE(2)
-  HFMM_M2L_TMA_CASE(3)
-  HFMM_M2L_TMA_CASE(4)
-  HFMM_M2L_TMA_CASE(6)
-#undef HFMM_M2L_TMA_CASE
+  if (nsplit > 1)
+    k_m2l_reduce<T><<<nt, 128, 0, s>>>(d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev, part,
+                                       pstride, nsplit);
+  count_launches(nsplit > 1 ? 2 : 1);
+  return hfmm_last_launch();
+}
+
+template <typename T, int CM>
+int launch_m2l_tma(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
+                   cudaStream_t s) {
+  const int P = t->P;
+  if (P <= 16) return launch_m2l_tma_rt<T, CM, 1, 16>(t, d, ops, src_set, tgt_set, s);
+  if (P <= 32) return launch_m2l_tma_rt<T, CM, 2, 16>(t, d, ops, src_set, tgt_set, s);
+  if (P <= 36) return launch_m2l_tma_rt<T, CM, 3, 12>(t, d, ops, src_set, tgt_set, s);
+  if (P <= 48) return launch_m2l_tma_rt<T, CM, 3, 16>(t, d, ops, src_set, tgt_set, s);
+  if (P <= 64) return launch_m2l_tma_rt<T, CM, 4, 16>(t, d, ops, src_set, tgt_set, s);
+  if (P <= 96) return launch_m2l_tma_rt<T, CM, 6, 16>(t, d, ops, src_set, tgt_set, s);
   return HFMM_ERR_UNSUPPORTED;
 }
 
@@ -1058,7 +1308,7 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   tm.begin(HFMM_STAGE_M2L, s);
   int nm2l = 0;
   const bool tiled = (sizeof(T) == 4 && P <= 81) || (sizeof(T) == 8 && P <= 64);
-  const bool tma = tiled && ((size_t)P * sizeof(C<T>)) % 16 == 0;
+  const bool tma = tiled && (P % 2 == 0);  // rows are 16-byte multiples; pairs of columns per load
   if (tma) {
     int st;
     if (t->m2l_tc == 32)

@@ -81,8 +81,11 @@ __global__ void k_gaunt(int p, double* gt) {
 }
 
 // One block per (operator, level).  vec(op, level) gives t; kind 0 = R, 1 = S.
-// Column-major storage: entry (a', a) at out[(level * nops + op) * P * P + a * P + a'],
-// so that threads owning consecutive output rows a' read consecutive words.
+// M2M / L2L are stored column-major: entry (a', a) at
+// out[(level * nops + op) * P * P + a * P + a'] (threads owning consecutive
+// output rows read consecutive words); M2L operators row-major, entry (a', a)
+// at ... + a' * P + a (a thread owning a row reads pairs of consecutive
+// columns with one 16-byte load).
 struct OpSet {
   int kind;     // 0: regular (j_l), 1: singular (h_l)
   int nops;     // operators per level
@@ -154,7 +157,14 @@ __global__ void k_translation(int p, double k, int lmin, OpSet set, const double
   __syncthreads();
   double2* T = out + ((int64_t)blockIdx.y * set.nops + op) * P * P;
   for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
-    int a = e / P, ap = e % P;
+    int a, ap;
+    if (set.mode == 0) {
+      ap = e / P;
+      a = e % P;
+    } else {
+      a = e / P;
+      ap = e % P;
+    }
     int n, m, np_, mp;
     nm_of(a, n, m);
     nm_of(ap, np_, mp);

@@ -236,11 +236,22 @@ __global__ void k_m2l_cells(const int* flags, const int64_t* level_off_dev, int*
   const int64_t off = level_off_dev[l];
   const int per = 1 << (3 * (l - 1));
   int* cells = cells_all + (mask - 1) * cells_stride + off + (int64_t)b * per;
+  // grouped by the first cube face the cell touches (x=0, x=1, y=0, y=1,
+  // z=0, z=1, none), Morton order within a group: cells of one tile then
+  // share most of their far-field source pattern when only boundary cells
+  // hold sources
+  const int sl = 1 << l;
   int c = 0;
-  for (int j = 0; j < per; ++j) {
-    int cell = 8 * j + b;
-    if (flags[off + cell] & mask) cells[c++] = cell;
-  }
+  for (int g = 0; g < 7; ++g)
+    for (int j = 0; j < per; ++j) {
+      int cell = 8 * j + b;
+      if (!(flags[off + cell] & mask)) continue;
+      int ix, iy, iz;
+      morton_decode((uint64_t)cell, ix, iy, iz);
+      int key = ix == 0 ? 0 : ix == sl - 1 ? 1 : iy == 0 ? 2 : iy == sl - 1 ? 3 : iz == 0 ? 4
+                : iz == sl - 1 ? 5 : 6;
+      if (key == g) cells[c++] = cell;
+    }
   counts[((mask - 1) * (HFMM_MAX_LEVEL + 1) + l) * 8 + b] = c;
 }
 

@@ -117,8 +117,15 @@ struct fmm_tree {
   int* m2l_cells[3] = {nullptr, nullptr, nullptr};
   int4* m2l_tiles[3] = {nullptr, nullptr, nullptr};
   int m2l_ntiles[3] = {0, 0, 0};
+  // per (target mask, source mask) pair, index 3 (tm-1) + (sm-1): the valid
+  // offsets of every tile (built on first use)
+  int* m2l_vlist[9] = {};
+  unsigned* m2l_vmask[9] = {};
+  int* m2l_nval[9] = {};
+  void* zero_row = nullptr;     // P complex zeros (bulk-copy source for empty columns)
   void* m2l_part = nullptr;     // [m2l_part_max][total_cells][P] split-offset partial sums
   int m2l_part_max = 1;
+  int m2l_variant = 1;          // 1: warp-specialised pipeline, 0: two-stage block pipeline
 
   // ---- operators (FP64 master copy; FP32 copy for the FP32 form)
   double2* op_m2m = nullptr;    // [L+1][8][P][P]   row a' (out), column a (in)
