@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--inner-rtol", type=float, default=1e-2)
+    ap.add_argument("--inner-maxit", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -246,7 +247,8 @@ def run_ours(args, world, rank, local):
     dev = torch.device(f"cuda:{local}")
     w = inputs.WORKLOADS[args.workload]
     n = w["n"]
-    gm = dict(restart=w["restart"], rtol=1e-6, inner_rtol=args.inner_rtol, inner_maxit=200, inner_m=50)
+    gm = dict(restart=w["restart"], rtol=1e-6, inner_rtol=args.inner_rtol, inner_maxit=args.inner_maxit,
+              inner_m=args.inner_maxit)
 
     t0 = time.perf_counter()
     tree = hfmm.Tree(n, w["k"], w["p"], w["theta"], w["leaf"], args.precision)
@@ -389,6 +391,7 @@ def run_ours(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "k": w["k"], "p": w["p"], "leaf": w["leaf"],
                        "theta": w["theta"], "restart": w["restart"], "inner_rtol": args.inner_rtol,
+                       "inner_maxit": args.inner_maxit,
                        "fmm_precision": args.precision, "krylov_precision": "fp64",
                        "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
