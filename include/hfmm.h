@@ -227,6 +227,36 @@ int fmm_get_stats(const fmm_tree* tree, hfmm_stats* stats);
  */
 int fmm_set_timing(fmm_tree* tree, int enable);
 
+/*
+ * hfmm_direct_sum_noalloc -- allocation-free direct Helmholtz sum.
+ *
+ * The paper has no counterpart to this entry point.  It exists for callers
+ * that cannot allocate device memory (a host framework that forbids
+ * cudaMalloc, an allocation-free real-time path, ...).  It allocates nothing:
+ * its only scratch space, the partial sums of the source chunks, is a fixed
+ * array inside the library (2^18 complex128 entries = 4 MiB, held by every
+ * device that loads the library until the process exits).
+ *
+ *   phi_i = sum_{j : |x_i - y_j| > 0} q_j exp(i k |x_i - y_j|) / (4 pi |x_i - y_j|)
+ *
+ *   n_src, d_src_xyz, d_q   sources: AoS x,y,z float64 and complex128 weights (device)
+ *   n_tgt, d_tgt_xyz        targets: AoS x,y,z float64 (device)
+ *   k                       wavenumber (>= 0)
+ *   d_phi                   n_tgt complex128 outputs (device), overwritten
+ * Limits: n_tgt <= 262144 (larger sizes return HFMM_ERR_INVALID_ARG and
+ * nothing is launched); the source set is split into at most
+ * min(32, 262144 / n_tgt) chunks.  FP64 arithmetic, deterministic.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  Calls share the scratch array, so calls that overlap on
+ * the GPU (different streams, or different host threads on one device) race
+ * and must be serialised by the caller.  Every scratch entry a call reads is
+ * written earlier in the same call, so no clearing is needed.
+ */
+int hfmm_direct_sum_noalloc(int64_t n_src, const double* d_src_xyz, const void* d_q,
+                            int64_t n_tgt, const double* d_tgt_xyz, double k, void* d_phi,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

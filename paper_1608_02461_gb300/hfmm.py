@@ -81,7 +81,13 @@ SIGNATURES = {
                                    ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
     "fmm_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hfmm_stats)]),
     "fmm_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hfmm_direct_sum_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
 }
+
+# scratch limit of hfmm_direct_sum_noalloc (targets)
+NOALLOC_MAX_TARGETS = 1 << 18
 
 _lib = None
 
@@ -248,3 +254,12 @@ class Tree:
         s = hfmm_stats()
         _check(lib().fmm_get_stats(self._h, ctypes.byref(s)), "fmm_get_stats")
         return s
+
+
+def direct_sum_noalloc(src_xyz, q, tgt_xyz, k, phi, stream=None):
+    """Allocation-free direct sum (hfmm_direct_sum_noalloc) into the caller's
+    complex128 tensor `phi`; all arguments are CUDA tensors."""
+    st = lib().hfmm_direct_sum_noalloc(src_xyz.shape[0], _ptr(src_xyz), _ptr(q), tgt_xyz.shape[0],
+                                       _ptr(tgt_xyz), float(k), _ptr(phi), _stream_ptr(stream))
+    _check(st, "hfmm_direct_sum_noalloc")
+    return phi
