@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--apply-only", nargs=2, type=int, metavar=("SRC", "TGT"),
+                    help="profiling case: build the tree and run two FMM applies with these "
+                         "source/target set masks (1 volume, 2 boundary, 3 both), print nothing else")
     return ap.parse_args()
 
 
@@ -412,9 +415,30 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_apply_only(args):
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_1608_02461_gb300 import hfmm, inputs
+    w = inputs.WORKLOADS[args.workload]
+    n = w["n"]
+    dev = torch.device("cuda:0")
+    tree = hfmm.Tree(n, w["k"], w["p"], w["theta"], w["leaf"], args.precision)
+    qv = torch.from_numpy(inputs.complex_normal(n ** 3, 1)).to(dev)
+    qb = torch.from_numpy(inputs.complex_normal(6 * n * n, 2)).to(dev)
+    src, tgt = args.apply_only
+    for _ in range(2):
+        tree.apply(qv, qb, src=src, tgt=tgt)
+    torch.cuda.synchronize()
+    tree.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
+    if args.apply_only:
+        run_apply_only(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
