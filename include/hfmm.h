@@ -56,6 +56,8 @@ extern "C" {
 
 /* fmm_apply modes */
 #define HFMM_FWD 0       /* phi = G~ q                                   */
+#define HFMM_ADJ 1       /* phi = G~^H q  (conjugate transpose)          */
+#define HFMM_DK  2       /* phi = d(G~ q)/dk                             */
 
 typedef struct hfmm_params {
     int p;            /* expansion order: degrees 0..p-1 (1 <= p <= 16)  */
@@ -161,14 +163,26 @@ void fmm_destroy_tree(fmm_tree* tree);
  * integral of G over the point's own cell divided by h^3 (interior node) or
  * over its own panel divided by h^2 (boundary element); zero for explicit
  * points.  Weights are used as given (no quadrature weight is applied).
+ * Call this linear map G~ (the truncated FMM operator from src_set to
+ * tgt_set).  `mode` selects:
+ *   HFMM_FWD  phi = G~ q:        q on src_set, phi on tgt_set
+ *   HFMM_ADJ  phi = G~^H q:      q on tgt_set, phi on src_set.  Every FMM
+ *             stage is conjugate-transposed and applied in reverse order
+ *             (L2P^H, L2L^H, M2L^H, M2M^H, P2M^H, conj(P2P), conj(self)),
+ *             so <G~ x, y> = <x, G~^H y> holds to rounding.
+ *   HFMM_DK   phi = dG~/dk q:    q on src_set, phi on tgt_set; the exact
+ *             k-derivative of the truncated FMM (tangent of every stage:
+ *             Bessel functions in P2M/L2P, translation operators, near-field
+ *             kernel, self terms).
  *
  *   src_set, tgt_set  non-zero OR of HFMM_SET_VOL / HFMM_SET_BND
- *   d_q_vol, d_q_bnd  source weights (complex128) per set; a set not in
- *                     src_set may be NULL
- *   d_phi_vol, d_phi_bnd  outputs (complex128) per set in tgt_set
- *                     (overwritten); a set not in tgt_set may be NULL
- *   mode              HFMM_FWD
- * Errors: INVALID_ARG, CUDA.
+ *   d_q_vol, d_q_bnd  input weights (complex128) per set of the input side;
+ *                     a set not on that side may be NULL
+ *   d_phi_vol, d_phi_bnd  outputs (complex128) per set of the output side
+ *                     (overwritten); a set not on that side may be NULL
+ * The adjoint and derivative operators are built on the first call in those
+ * modes (device memory held by the handle).
+ * Errors: INVALID_ARG, NOMEM, CUDA.
  */
 int fmm_apply(fmm_tree* tree, int src_set, int tgt_set,
               const void* d_q_vol, const void* d_q_bnd,

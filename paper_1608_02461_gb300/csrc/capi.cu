@@ -39,6 +39,8 @@ void release(fmm_tree* t) {
   if (t->ev0) cudaEventDestroy(t->ev0);
   if (t->ev1) cudaEventDestroy(t->ev1);
   t->timer.destroy();
+  if (t->gaunt) cudaFree(t->gaunt);
+  t->gaunt = nullptr;
 }
 
 fmm_tree_ext* ext_of(fmm_tree* t) { return t->ext; }
@@ -209,16 +211,26 @@ extern "C" int fmm_apply(fmm_tree* t, int src_set, int tgt_set, const void* d_q_
   if (!t) return HFMM_ERR_INVALID_ARG;
   const int all = HFMM_SET_VOL | HFMM_SET_BND;
   if (src_set <= 0 || (src_set & ~all) || tgt_set <= 0 || (tgt_set & ~all)) return HFMM_ERR_INVALID_ARG;
-  if (mode != HFMM_FWD) return HFMM_ERR_UNSUPPORTED;
-  if ((src_set & HFMM_SET_VOL) && !d_q_vol) return HFMM_ERR_INVALID_ARG;
-  if ((src_set & HFMM_SET_BND) && t->n_bnd > 0 && !d_q_bnd) return HFMM_ERR_INVALID_ARG;
-  if ((tgt_set & HFMM_SET_VOL) && !d_phi_vol) return HFMM_ERR_INVALID_ARG;
-  if ((tgt_set & HFMM_SET_BND) && t->n_bnd > 0 && !d_phi_bnd) return HFMM_ERR_INVALID_ARG;
+  if (mode != HFMM_FWD && mode != HFMM_ADJ && mode != HFMM_DK) return HFMM_ERR_INVALID_ARG;
+  const int in_set = mode == HFMM_ADJ ? tgt_set : src_set;
+  const int out_set = mode == HFMM_ADJ ? src_set : tgt_set;
+  if ((in_set & HFMM_SET_VOL) && !d_q_vol) return HFMM_ERR_INVALID_ARG;
+  if ((in_set & HFMM_SET_BND) && t->n_bnd > 0 && !d_q_bnd) return HFMM_ERR_INVALID_ARG;
+  if ((out_set & HFMM_SET_VOL) && !d_phi_vol) return HFMM_ERR_INVALID_ARG;
+  if ((out_set & HFMM_SET_BND) && t->n_bnd > 0 && !d_phi_bnd) return HFMM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   HFMM_CUDA_TRY(cudaEventRecord(t->ev0, s));
-  HFMM_TRY(fmm_gather(t, src_set, (const double2*)d_q_vol, 1.0, (const double2*)d_q_bnd, 1.0, s));
-  HFMM_TRY(fmm_core(t, src_set, tgt_set, s));
-  HFMM_TRY(fmm_scatter(t, tgt_set, (double2*)d_phi_vol, (double2*)d_phi_bnd, s));
+  HFMM_TRY(fmm_gather(t, in_set, (const double2*)d_q_vol, 1.0, (const double2*)d_q_bnd, 1.0, s));
+  if (mode == HFMM_FWD) {
+    HFMM_TRY(fmm_core(t, src_set, tgt_set, s));
+    HFMM_TRY(fmm_scatter(t, out_set, (double2*)d_phi_vol, (double2*)d_phi_bnd, s));
+  } else if (mode == HFMM_ADJ) {
+    HFMM_TRY(fmm_core_adjoint(t, src_set, tgt_set, s));
+    HFMM_TRY(fmm_scatter(t, out_set, (double2*)d_phi_vol, (double2*)d_phi_bnd, s));
+  } else {
+    HFMM_TRY(fmm_core_dk(t, src_set, tgt_set, s));
+    HFMM_TRY(fmm_scatter_from(t, t->phis_d, out_set, (double2*)d_phi_vol, (double2*)d_phi_bnd, s));
+  }
   HFMM_CUDA_TRY(cudaEventRecord(t->ev1, s));
   return HFMM_OK;
 }

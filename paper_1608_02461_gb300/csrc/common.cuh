@@ -81,15 +81,15 @@ __host__ __device__ __forceinline__ void morton_decode(uint64_t m, int& ix, int&
 
 // ---------------------------------------------------------------- error plumbing
 
-#define HFMM_CUDA_TRY(expr)                              \
+#define HFMM_CUDA_TRY(...)                               \
   do {                                                   \
-    cudaError_t _e = (expr);                             \
+    cudaError_t _e = (__VA_ARGS__);                      \
     if (_e != cudaSuccess) return HFMM_ERR_CUDA;         \
   } while (0)
 
-#define HFMM_TRY(expr)                                   \
+#define HFMM_TRY(...)                                    \
   do {                                                   \
-    int _s = (expr);                                     \
+    int _s = (__VA_ARGS__);                              \
     if (_s != HFMM_OK) return _s;                        \
   } while (0)
 

@@ -96,13 +96,45 @@ __device__ __forceinline__ void local_coords(const FmmDev<T>& d, int i, int leaf
 // ---------------------------------------------------------------- P2M
 // one block per leaf; CHUNK points' basis rows staged in shared memory, then
 // summed per coefficient
+// conj(dR_a/dk)(v) * q = |v| j_n'(k|v|) conj(Y_a(v^)) * q for all a < P, with
+// (2n+1) j_n' = n j_{n-1} - (n+1) j_{n+1} (no division by k|v|)
 template <typename T>
-__global__ void k_p2m(FmmDev<T> d, int64_t leaf_off, int src_set, int chunk) {
+__device__ void regular_basis_dk_conj(int p, T k, T dx, T dy, T dz, C<T> q, C<T>* out) {
+  T r, ct, st, cp, sp;
+  direction<T>(dx, dy, dz, r, ct, st, cp, sp);
+  T jn[HFMM_MAX_P + 1];
+  T pl[HFMM_MAX_P * (HFMM_MAX_P + 1) / 2];
+  sph_bessel_j<T>(k * r, p + 1, jn);
+  legendre_bar<T>(ct, st, p, pl);
+  T er = T(1), ei = T(0);
+  for (int m = 0; m < p; ++m) {
+    for (int n = m; n < p; ++n) {
+      T djn = (n > 0 ? T(n) * jn[n - 1] : T(0)) - T(n + 1) * jn[n + 1];
+      djn = r * djn / T(2 * n + 1);
+      T v = djn * pl[n * (n + 1) / 2 + m];
+      C<T> R = mkc<T>(v * er, v * ei);
+      out[n * n + n + m] = cmul<T>(conjc<T>(R), q);
+      if (m > 0) {
+        C<T> Rm = (m & 1) ? mkc<T>(-R.x, -R.y) : R;
+        out[n * n + n - m] = cmul<T>(Rm, q);
+      }
+    }
+    T nr = er * cp - ei * sp, ni = er * sp + ei * cp;
+    er = nr;
+    ei = ni;
+  }
+}
+
+// one block per leaf; CHUNK points' basis rows staged in shared memory, then
+// summed per coefficient.  Output Mout (leaf level), weights times `fac`;
+// DK: derivative of the basis with respect to k.
+template <typename T, bool DK>
+__global__ void k_p2m(FmmDev<T> d, C<T>* Mout, int64_t leaf_off, int src_set, int chunk, C<T> fac) {
   extern __shared__ unsigned char smem_raw[];
   C<T>* basis = reinterpret_cast<C<T>*>(smem_raw);
   const int leaf = blockIdx.x;
   const int P = d.P;
-  C<T>* M = d.M + (leaf_off + leaf) * P;
+  C<T>* M = Mout + (leaf_off + leaf) * P;
   int lo, hi;
   leaf_range(d.leaf_start, d.leaf_mid, leaf, src_set, lo, hi);
   if (hi <= lo) {
@@ -118,7 +150,11 @@ __global__ void k_p2m(FmmDev<T> d, int64_t leaf_off, int src_set, int chunk) {
       if (j < hi) {
         T dx, dy, dz;
         local_coords<T>(d, j, leaf, dx, dy, dz);
-        regular_basis<T, true>(d.p, d.k, dx, dy, dz, d.qs[j], row);
+        C<T> q = cmul<T>(d.qs[j], fac);
+        if constexpr (DK)
+          regular_basis_dk_conj<T>(d.p, d.k, dx, dy, dz, q, row);
+        else
+          regular_basis<T, true>(d.p, d.k, dx, dy, dz, q, row);
       } else {
         for (int a = 0; a < P; ++a) row[a] = mkc<T>(0, 0);
       }
@@ -148,21 +184,22 @@ __device__ __forceinline__ C<T> matvec_row(const C<T>* Tcol, int ap, const C<T>*
 }
 
 template <typename T>
-__global__ void k_m2m(FmmDev<T> d, int level, int64_t off_par, int64_t off_child, const C<T>* ops,
-                      int src_set) {
+__global__ void k_m2m(FmmDev<T> d, int level, int64_t off_par, int64_t off_child, const C<T>* Min, C<T>* Mout,
+                      const C<T>* ops, int src_set, int accumulate) {
   extern __shared__ unsigned char smem_raw[];
   C<T>* xs = reinterpret_cast<C<T>*>(smem_raw);
   const int cell = blockIdx.x;
   const int P = d.P;
-  C<T>* Mp = d.M + (off_par + cell) * P;
+  C<T>* Mp = Mout + (off_par + cell) * P;
   if (!(d.flags[off_par + cell] & src_set)) {
-    for (int a = threadIdx.x; a < P; a += blockDim.x) Mp[a] = mkc<T>(0, 0);
+    if (!accumulate)
+      for (int a = threadIdx.x; a < P; a += blockDim.x) Mp[a] = mkc<T>(0, 0);
     return;
   }
-  for (int e = threadIdx.x; e < 8 * P; e += blockDim.x) xs[e] = d.M[(off_child + 8 * (int64_t)cell) * P + e];
+  for (int e = threadIdx.x; e < 8 * P; e += blockDim.x) xs[e] = Min[(off_child + 8 * (int64_t)cell) * P + e];
   __syncthreads();
   for (int ap = threadIdx.x; ap < P; ap += blockDim.x) {
-    C<T> acc = mkc<T>(0, 0);
+    C<T> acc = accumulate ? Mp[ap] : mkc<T>(0, 0);
     for (int o = 0; o < 8; ++o) {
       C<T> v = matvec_row<T>(ops + (int64_t)o * P * P, ap, xs + o * P, P);
       acc = cadd<T>(acc, v);
@@ -171,17 +208,19 @@ __global__ void k_m2m(FmmDev<T> d, int level, int64_t off_par, int64_t off_child
   }
 }
 
+// Lout(child) += T_octant Lin(parent)
 template <typename T>
-__global__ void k_l2l(FmmDev<T> d, int64_t off_par, int64_t off_child, const C<T>* ops, int tgt_set) {
+__global__ void k_l2l(FmmDev<T> d, int64_t off_par, int64_t off_child, const C<T>* Lin, C<T>* Lout,
+                      const C<T>* ops, int tgt_set) {
   extern __shared__ unsigned char smem_raw[];
   C<T>* xs = reinterpret_cast<C<T>*>(smem_raw);
   const int cell = blockIdx.x;  // child
   const int P = d.P;
   if (!(d.flags[off_child + cell] & tgt_set)) return;
   const int parent = cell >> 3, o = cell & 7;
-  for (int e = threadIdx.x; e < P; e += blockDim.x) xs[e] = d.Lc[(off_par + parent) * P + e];
+  for (int e = threadIdx.x; e < P; e += blockDim.x) xs[e] = Lin[(off_par + parent) * P + e];
   __syncthreads();
-  C<T>* Lch = d.Lc + (off_child + cell) * P;
+  C<T>* Lch = Lout + (off_child + cell) * P;
   for (int ap = threadIdx.x; ap < P; ap += blockDim.x) {
     C<T> v = matvec_row<T>(ops + (int64_t)o * P * P, ap, xs, P);
     Lch[ap] = cadd<T>(Lch[ap], v);
@@ -193,7 +232,7 @@ __global__ void k_l2l(FmmDev<T> d, int64_t off_par, int64_t off_child, const C<T
 // T_{slot} M_S, sources skipped when they hold no point of the source set
 template <typename T>
 __global__ void k_m2l(FmmDev<T> d, int level, int64_t off, const C<T>* ops, const int* m2l_off,
-                      const int* m2l_slot, int m2l_count, int src_set, int tgt_set) {
+                      const int* m2l_slot, int m2l_count, int src_set, int tgt_set, int accumulate) {
   extern __shared__ unsigned char smem_raw[];
   C<T>* xs = reinterpret_cast<C<T>*>(smem_raw);
   const int cell = blockIdx.x;
@@ -226,7 +265,10 @@ __global__ void k_m2l(FmmDev<T> d, int level, int64_t off, const C<T>* ops, cons
   }
   for (int q = 0; q < 4; ++q) {
     int ap = threadIdx.x + q * blockDim.x;
-    if (ap < P) d.Lc[(off + cell) * P + ap] = acc[q];
+    if (ap < P) {
+      C<T>* dst = d.Lc + (off + cell) * P + ap;
+      *dst = accumulate ? cadd<T>(*dst, acc[q]) : acc[q];
+    }
   }
 }
 
@@ -244,7 +286,7 @@ __global__ void __launch_bounds__(128) k_m2l_tiled(FmmDev<T> d, const int4* __re
                                                    const C<T>* __restrict__ ops, int64_t box_cells,
                                                    const int* __restrict__ m2l_off,
                                                    const int* __restrict__ m2l_slot, int m2l_count,
-                                                   int src_set) {
+                                                   int src_set, int accumulate) {
   constexpr int CT = 8, RT = 16, TC = CT * CM;
   extern __shared__ unsigned char smem_raw[];
   const int P = d.P;
@@ -321,7 +363,10 @@ __global__ void __launch_bounds__(128) k_m2l_tiled(FmmDev<T> d, const int4* __re
 #pragma unroll
     for (int j = 0; j < CM; ++j) {
       int ap = r0 + r * RT, c = c0 + j * CT;
-      if (ap < P && c < cnt) d.Lc[(off + tcell[c]) * P + ap] = acc[r][j];
+      if (ap < P && c < cnt) {
+        C<T>* dst = d.Lc + (off + tcell[c]) * P + ap;
+        *dst = accumulate ? cadd<T>(*dst, acc[r][j]) : acc[r][j];
+      }
     }
 }
 
@@ -497,7 +542,7 @@ __global__ void __launch_bounds__(RT * 8) k_m2l_tma(FmmDev<T> d, const int4* __r
                                                     const unsigned* __restrict__ vmask_all,
                                                     const int* __restrict__ nval_all,
                                                     const C<T>* __restrict__ zero_row,
-                                                    C<T>* __restrict__ part, int64_t part_stride) {
+                                                    C<T>* __restrict__ part, int64_t part_stride, int accumulate) {
   constexpr int CT = 8, TC = CT * CM, NT = RT * CT;
   const int P = d.P;
   const int MS = P + 2;  // padded source row (16-byte multiple, spreads banks)
@@ -603,10 +648,12 @@ __global__ void __launch_bounds__(RT * 8) k_m2l_tma(FmmDev<T> d, const int4* __r
     for (int j = 0; j < CM; ++j) {
       int ap = r0 + r * RT, c = c0 + j * CT;
       if (ap < P && c < cnt) {
-        if (out)
+        if (out) {
           out[(int64_t)(first + c) * P + ap] = acc[r][j];
-        else
-          d.Lc[(off + tcell[c]) * P + ap] = acc[r][j];
+        } else {
+          C<T>* dst = d.Lc + (off + tcell[c]) * P + ap;
+          *dst = accumulate ? cadd<T>(*dst, acc[r][j]) : acc[r][j];
+        }
       }
     }
   (void)NT;
@@ -645,7 +692,7 @@ __global__ void __launch_bounds__(RT * 8 + 32) k_m2l_ws(FmmDev<T> d, const int4*
                                                         const unsigned* __restrict__ vmask_all,
                                                         const int* __restrict__ nval_all,
                                                         const C<T>* __restrict__ zero_row,
-                                                        C<T>* __restrict__ part, int64_t part_stride) {
+                                                        C<T>* __restrict__ part, int64_t part_stride, int accumulate) {
   constexpr int CT = 8, TC = CT * CM, NC = RT * CT, NCW = NC / 32;
   const int P = d.P;
   const int MS = P + 2;
@@ -753,10 +800,12 @@ __global__ void __launch_bounds__(RT * 8 + 32) k_m2l_ws(FmmDev<T> d, const int4*
         for (int j = 0; j < CM; ++j) {
           int ap = r0 + r * RT, c = c0 + j * CT;
           if (ap < P && c < cnt) {
-            if (out)
+            if (out) {
               out[(int64_t)(first + c) * P + ap] = acc[r][j];
-            else
-              d.Lc[(off + tcell[c]) * P + ap] = acc[r][j];
+            } else {
+              C<T>* dst = d.Lc + (off + tcell[c]) * P + ap;
+              *dst = accumulate ? cadd<T>(*dst, acc[r][j]) : acc[r][j];
+            }
           }
         }
     }
@@ -769,7 +818,7 @@ __global__ void __launch_bounds__(RT * 8 + 32) k_m2l_ws(FmmDev<T> d, const int4*
 template <typename T>
 __global__ void k_m2l_reduce(FmmDev<T> d, const int4* __restrict__ tiles, const int* __restrict__ cells,
                              const int64_t* __restrict__ level_off, const C<T>* __restrict__ part,
-                             int64_t part_stride, int nsplit) {
+                             int64_t part_stride, int nsplit, int accumulate) {
   const int4 tile = tiles[blockIdx.x];
   const int P = d.P;
   const int64_t off = level_off[tile.x];
@@ -778,7 +827,8 @@ __global__ void k_m2l_reduce(FmmDev<T> d, const int4* __restrict__ tiles, const 
     int64_t slot = (int64_t)(tile.z + c) * P + a;
     C<T> v = part[slot];
     for (int k = 1; k < nsplit; ++k) v = cadd<T>(v, part[k * part_stride + slot]);
-    d.Lc[(off + cells[tile.z + c]) * P + a] = v;
+    C<T>* dst = d.Lc + (off + cells[tile.z + c]) * P + a;
+    *dst = accumulate ? cadd<T>(*dst, v) : v;
   }
 }
 
@@ -801,7 +851,7 @@ int m2l_valid_lists(fmm_tree* t, int sm, int tm, cudaStream_t s) {
 
 template <typename T, int CM, int R, int RT>
 int launch_m2l_tma_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
-                      cudaStream_t s) {
+                      int accumulate, cudaStream_t s) {
   const int P = t->P, mi = tgt_set - 1;
   const int TC = 8 * CM;
   const int nt = t->m2l_ntiles[mi];
@@ -822,37 +872,37 @@ int launch_m2l_tma_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_
     k_m2l_ws<T, R, CM, RT, NSTG><<<dim3(nt, nsplit), RT * 8 + 32, smw, s>>>(
         d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev, ops, t->box_cells, t->m2l_off,
         t->m2l_box_index, t->m2l_count, t->m2l_vlist[ci], t->m2l_vmask[ci], t->m2l_nval[ci],
-        reinterpret_cast<const C<T>*>(t->zero_row), part, pstride);
+        reinterpret_cast<const C<T>*>(t->zero_row), part, pstride, accumulate);
   } else {
     HFMM_TRY(set_smem<T>((const void*)k_m2l_tma<T, R, CM, RT>, sm));
     k_m2l_tma<T, R, CM, RT><<<dim3(nt, nsplit), RT * 8, sm, s>>>(
         d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev, ops, t->box_cells, t->m2l_off,
         t->m2l_box_index, t->m2l_count, t->m2l_vlist[ci], t->m2l_vmask[ci], t->m2l_nval[ci],
-        reinterpret_cast<const C<T>*>(t->zero_row), part, pstride);
+        reinterpret_cast<const C<T>*>(t->zero_row), part, pstride, accumulate);
   }
   if (nsplit > 1)
     k_m2l_reduce<T><<<nt, 128, 0, s>>>(d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev, part,
-                                       pstride, nsplit);
+                                       pstride, nsplit, accumulate);
   count_launches(nsplit > 1 ? 2 : 1);
   return hfmm_last_launch();
 }
 
 template <typename T, int CM>
 int launch_m2l_tma(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
-                   cudaStream_t s) {
+                   int accumulate, cudaStream_t s) {
   const int P = t->P;
-  if (P <= 16) return launch_m2l_tma_rt<T, CM, 1, 16>(t, d, ops, src_set, tgt_set, s);
-  if (P <= 32) return launch_m2l_tma_rt<T, CM, 2, 16>(t, d, ops, src_set, tgt_set, s);
-  if (P <= 36) return launch_m2l_tma_rt<T, CM, 3, 12>(t, d, ops, src_set, tgt_set, s);
-  if (P <= 48) return launch_m2l_tma_rt<T, CM, 3, 16>(t, d, ops, src_set, tgt_set, s);
-  if (P <= 64) return launch_m2l_tma_rt<T, CM, 4, 16>(t, d, ops, src_set, tgt_set, s);
-  if (P <= 96) return launch_m2l_tma_rt<T, CM, 6, 16>(t, d, ops, src_set, tgt_set, s);
+  if (P <= 16) return launch_m2l_tma_rt<T, CM, 1, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 32) return launch_m2l_tma_rt<T, CM, 2, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 36) return launch_m2l_tma_rt<T, CM, 3, 12>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 48) return launch_m2l_tma_rt<T, CM, 3, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 64) return launch_m2l_tma_rt<T, CM, 4, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 96) return launch_m2l_tma_rt<T, CM, 6, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
   return HFMM_ERR_UNSUPPORTED;
 }
 
 template <typename T, int CM>
 int launch_m2l_tiled(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, const int64_t* level_off_dev,
-                     int src_set, int tgt_set, cudaStream_t s) {
+                     int src_set, int tgt_set, int accumulate, cudaStream_t s) {
   const int P = t->P, mi = tgt_set - 1;
   const int TC = 8 * CM;
   size_t sm = ((size_t)P * P + (size_t)P * (TC + 1)) * sizeof(C<T>) + 5 * TC * sizeof(int);
@@ -864,7 +914,7 @@ int launch_m2l_tiled(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, const int
     HFMM_TRY(set_smem<T>(fn, sm));                                      \
     k_m2l_tiled<T, RR, CM><<<t->m2l_ntiles[mi], 128, sm, s>>>(          \
         d, t->m2l_tiles[mi], t->m2l_cells[mi], level_off_dev, ops, t->box_cells, t->m2l_off, \
-        t->m2l_box_index, t->m2l_count, src_set);                       \
+        t->m2l_box_index, t->m2l_count, src_set, accumulate);           \
     return hfmm_last_launch();                                          \
   }
   HFMM_M2L_CASE(1)
@@ -877,8 +927,9 @@ int launch_m2l_tiled(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, const int
 }
 
 // ---------------------------------------------------------------- L2P
+// phi_i = fac * sum_a L_a R_a(x_i - c)   (forward fac = i k; adjoint fac = 1)
 template <typename T>
-__global__ void k_l2p(FmmDev<T> d, int64_t leaf_off, int tgt_set) {
+__global__ void k_l2p(FmmDev<T> d, int64_t leaf_off, int tgt_set, C<T> fac) {
   extern __shared__ unsigned char smem_raw[];
   C<T>* Ls = reinterpret_cast<C<T>*>(smem_raw);
   const int leaf = blockIdx.x;
@@ -914,8 +965,69 @@ __global__ void k_l2p(FmmDev<T> d, int64_t leaf_off, int tgt_set) {
       er = nr;
       ei = ni;
     }
-    // phi = i k acc
-    d.phis[i] = mkc<T>(-d.k * acc.y, d.k * acc.x);
+    d.phis[i] = cmul<T>(fac, acc);
+  }
+}
+
+// d(phi_i)/dk = sum_a [(i L_a + i k dL_a) R_a + i k L_a dR_a/dk],
+// dR_a/dk = |v| j_n'(k|v|) Y_a (tangent of L2P, written to `out`)
+template <typename T>
+__global__ void k_l2p_dk(FmmDev<T> d, const C<T>* __restrict__ Lv, const C<T>* __restrict__ Ldv,
+                         C<T>* __restrict__ out, int64_t leaf_off, int tgt_set) {
+  extern __shared__ unsigned char smem_raw[];
+  C<T>* Ls = reinterpret_cast<C<T>*>(smem_raw);
+  const int leaf = blockIdx.x;
+  const int P = d.P;
+  int lo, hi;
+  leaf_range(d.leaf_start, d.leaf_mid, leaf, tgt_set, lo, hi);
+  if (hi <= lo) return;
+  C<T>* Lds = Ls + P;
+  for (int e = threadIdx.x; e < P; e += blockDim.x) {
+    Ls[e] = Lv[(leaf_off + leaf) * P + e];
+    Lds[e] = Ldv[(leaf_off + leaf) * P + e];
+  }
+  __syncthreads();
+  const T k = d.k;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    T dx, dy, dz;
+    local_coords<T>(d, i, leaf, dx, dy, dz);
+    T r, ct, st, cp, sp;
+    direction<T>(dx, dy, dz, r, ct, st, cp, sp);
+    T jn[HFMM_MAX_P + 1];
+    T pl[HFMM_MAX_P * (HFMM_MAX_P + 1) / 2];
+    sph_bessel_j<T>(k * r, d.p + 1, jn);
+    legendre_bar<T>(ct, st, d.p, pl);
+    C<T> a1 = mkc<T>(0, 0), a2 = mkc<T>(0, 0), a3 = mkc<T>(0, 0);  // L.R, dL.R, L.dR
+    T er = T(1), ei = T(0);
+    for (int m = 0; m < d.p; ++m) {
+      for (int n = m; n < d.p; ++n) {
+        T pv = pl[n * (n + 1) / 2 + m];
+        T v = jn[n] * pv;
+        T djn = r * ((n > 0 ? T(n) * jn[n - 1] : T(0)) - T(n + 1) * jn[n + 1]) / T(2 * n + 1);
+        T dv = djn * pv;
+        C<T> R = mkc<T>(v * er, v * ei), dR = mkc<T>(dv * er, dv * ei);
+        const int ap = n * n + n + m, am = n * n + n - m;
+        cfma<T>(a1, Ls[ap], R);
+        cfma<T>(a2, Lds[ap], R);
+        cfma<T>(a3, Ls[ap], dR);
+        if (m > 0) {
+          C<T> Rc = conjc<T>(R), dRc = conjc<T>(dR);
+          if (m & 1) {
+            Rc = mkc<T>(-Rc.x, -Rc.y);
+            dRc = mkc<T>(-dRc.x, -dRc.y);
+          }
+          cfma<T>(a1, Ls[am], Rc);
+          cfma<T>(a2, Lds[am], Rc);
+          cfma<T>(a3, Ls[am], dRc);
+        }
+      }
+      T nr = er * cp - ei * sp, ni = er * sp + ei * cp;
+      er = nr;
+      ei = ni;
+    }
+    // i a1 + i k (a2 + a3)
+    C<T> s = mkc<T>(a1.x + k * (a2.x + a3.x), a1.y + k * (a2.y + a3.y));
+    out[i] = mkc<T>(-s.y, s.x);
   }
 }
 
@@ -1052,7 +1164,8 @@ __device__ __forceinline__ T rsqrt_t(T x) {
   else return rsqrtf(x);
 }
 
-template <typename T, int W>
+// KMODE 0: G = e^{ikr}/(4 pi r); 1: conj(G) (adjoint); 2: dG/dk = i e^{ikr}/(4 pi) (tangent)
+template <typename T, int W, int KMODE>
 __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restrict__ near_off,
                                                 int near_count, int src_set, int tgt_set,
                                                 double2 sig_vol, double2 sig_bnd) {
@@ -1167,9 +1280,20 @@ __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restri
           T sn, cs;
           sincos_kr<T>(k * r, sn, cs);
           const C<T> q = sq[e];
-          const T wr = q.x * rinv, wi = q.y * rinv;
-          part.x = fma(cs, wr, fma(-sn, wi, part.x));
-          part.y = fma(cs, wi, fma(sn, wr, part.y));
+          if constexpr (KMODE == 0) {
+            const T wr = q.x * rinv, wi = q.y * rinv;
+            part.x = fma(cs, wr, fma(-sn, wi, part.x));
+            part.y = fma(cs, wi, fma(sn, wr, part.y));
+          } else if constexpr (KMODE == 1) {
+            const T wr = q.x * rinv, wi = q.y * rinv;
+            part.x = fma(cs, wr, fma(sn, wi, part.x));
+            part.y = fma(cs, wi, fma(-sn, wr, part.y));
+          } else {  // i e^{ikr} q (zero-distance pairs masked through rinv)
+            const T m = rinv > T(0) ? T(1) : T(0);
+            const T gr = -sn * m, gi = cs * m;
+            part.x = fma(gr, q.x, fma(-gi, q.y, part.x));
+            part.y = fma(gr, q.y, fma(gi, q.x, part.y));
+          }
         }
       }
       if constexpr (sizeof(T) == 4) {
@@ -1271,6 +1395,182 @@ int set_smem(const void* fn, size_t bytes) {
   return HFMM_OK;
 }
 
+// M2L over all levels with the kernel that fits P and the precision;
+// reads d.M, writes (or adds to) d.Lc
+template <typename T>
+int m2l_stage(fmm_tree* t, const FmmDev<T>& d, const C<T>* m2l, int src_set, int tgt_set, int accumulate,
+              cudaStream_t s, int* nlaunch) {
+  const int P = t->P, L = t->L;
+  const int64_t PP = (int64_t)P * P;
+  const bool tiled = (sizeof(T) == 4 && P <= 81) || (sizeof(T) == 8 && P <= 64);
+  const bool tma = tiled && (P % 2 == 0);  // rows are 16-byte multiples; pairs of columns per load
+  if (tma) {
+    *nlaunch = 0;  // counted by the launcher
+    if (t->m2l_tc == 32) return launch_m2l_tma<T, 4>(t, d, m2l, src_set, tgt_set, accumulate, s);
+    return launch_m2l_tma<T, 2>(t, d, m2l, src_set, tgt_set, accumulate, s);
+  }
+  if (tiled) {
+    *nlaunch = 1;
+    if (t->m2l_tc == 32)  // tiles hold up to 32 cells: 8 column groups x 4
+      return launch_m2l_tiled<T, 4>(t, d, m2l, t->level_off_dev, src_set, tgt_set, accumulate, s);
+    return launch_m2l_tiled<T, 2>(t, d, m2l, t->level_off_dev, src_set, tgt_set, accumulate, s);
+  }
+  const int th = threads_for(P);
+  const size_t sm1 = (size_t)P * sizeof(C<T>);
+  for (int l = 2; l <= L; ++l)
+    k_m2l<T><<<1 << (3 * l), th, sm1, s>>>(d, l, t->level_off[l], m2l + (int64_t)l * t->box_cells * PP,
+                                            t->m2l_off, t->m2l_box_index, t->m2l_count, src_set, tgt_set,
+                                            accumulate);
+  *nlaunch = L - 1;
+  return hfmm_last_launch();
+}
+
+template <typename T, int KMODE>
+int p2p_stage(fmm_tree* t, const FmmDev<T>& d, int src_set, int tgt_set, double2 sv, double2 sb,
+              cudaStream_t s) {
+  const int nleaf = 1 << (3 * t->L);
+  if (t->near_count <= 128) {
+    k_p2p_v2<T, (sizeof(T) == 4 ? 1536 : 768), KMODE><<<nleaf, 256, 0, s>>>(d, t->near_off, t->near_count,
+                                                                            src_set, tgt_set, sv, sb);
+    return hfmm_last_launch();
+  }
+  if (KMODE != 0) return HFMM_ERR_UNSUPPORTED;
+  k_p2p<T><<<nleaf, 128, 0, s>>>(d, t->near_off, t->near_count, src_set, tgt_set, sv, sb);
+  return hfmm_last_launch();
+}
+
+template <typename T>
+const C<T>* ops_of(const fmm_tree* t, const double2* o64, const float2* o32) {
+  return reinterpret_cast<const C<T>*>(sizeof(T) == 4 ? (const void*)o32 : (const void*)o64);
+}
+
+// Adjoint pass (every stage conjugate-transposed, in reverse order).  The
+// weights y in qs live on the forward targets (tgt_set); the result on the
+// forward sources (src_set) goes to phis.  With S' = tgt_set, T' = src_set:
+//   Lh_L  = (-i k) P2M(y)                       (L2P^H)
+//   Lh_l  = sum_o L2L_o^H Lh_{l+1}              (L2L^H, upward)
+//   Mh_l  = M2L^H Lh_l                          (slot of -v, conjugate transpose)
+//   Mh_{l+1} += M2M_o^H Mh_l                    (M2M^H, downward)
+//   phi   = L2P(Mh_L) without the i k factor    (P2M^H)
+//   phi  += conj(G) y near field + conj(s) y    (P2P^H, self term)
+template <typename T>
+int core_adjoint_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
+  HFMM_TRY(build_operators_adjoint(t, s));
+  FmmDev<T> d = make_dev<T>(t);
+  const int P = t->P, L = t->L;
+  const int nleaf = 1 << (3 * L);
+  const int64_t PP = (int64_t)P * P;
+  const int th = threads_for(P);
+  const C<T>* m2m_h = ops_of<T>(t, t->op_m2m_h, t->op_m2m_h32);
+  const C<T>* l2l_h = ops_of<T>(t, t->op_l2l_h, t->op_l2l_h32);
+  const C<T>* m2l_h = ops_of<T>(t, t->op_m2l_h, t->op_m2l_h32);
+  C<T>* Lh = d.Lc;  // cotangents of the local expansions
+  C<T>* Mh = d.M;   // cotangents of the multipole expansions
+  const int Sp = tgt_set, Tp = src_set;
+  const int chunk = 32;
+  size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
+  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
+  k_p2m<T, false><<<nleaf, 64, sm_p2m, s>>>(d, Lh, t->level_off[L], Sp, chunk, mkc<T>(0, -d.k));
+  size_t sm8 = 8 * (size_t)P * sizeof(C<T>);
+  HFMM_TRY(set_smem<T>((const void*)k_m2m<T>, sm8));
+  for (int l = L - 1; l >= 2; --l)
+    k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], Lh, Lh,
+                                            l2l_h + (int64_t)l * 8 * PP, Sp, 0);
+  FmmDev<T> dm = d;
+  dm.M = Lh;
+  dm.Lc = Mh;
+  int nm = 0;
+  HFMM_TRY(m2l_stage<T>(t, dm, m2l_h, Sp, Tp, 0, s, &nm));
+  size_t sm1 = (size_t)P * sizeof(C<T>);
+  for (int l = 2; l < L; ++l)
+    k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], Mh, Mh,
+                                                  m2m_h + (int64_t)l * 8 * PP, Tp);
+  FmmDev<T> dl = d;
+  dl.Lc = Mh;
+  k_l2p<T><<<nleaf, 64, sm1, s>>>(dl, t->level_off[L], Tp, mkc<T>(1, 0));
+  const double2 cv = make_double2(t->sigma_vol.x, -t->sigma_vol.y);
+  const double2 cb = make_double2(t->sigma_bnd.x, -t->sigma_bnd.y);
+  HFMM_TRY(p2p_stage<T, 1>(t, d, Sp, Tp, cv, cb, s));
+  count_launches(4 + 2 * (L > 2 ? L - 2 : 0) + nm);
+  return hfmm_last_launch();
+}
+
+// Tangent pass: d(phi)/dk for fixed weights q (in qs), into phis_d.
+//   M, dM  = P2M(q), P2M_k(q)
+//   dM_l   = T dM_{l+1} + dT M_{l+1}            (M2M)
+//   dL_l   = T dM + dT M                        (M2L)
+//   dL_{l+1} += T dL_l + dT L_l                 (L2L)
+//   dphi   = i L.R + i k dL.R + i k L.dR        (L2P)
+//   dphi  += dG/dk near field + ds/dk q          (P2P, self term)
+template <typename T>
+int core_dk_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
+  HFMM_TRY(build_operators_deriv(t, s));
+  const int P = t->P, L = t->L;
+  const size_t csz = sizeof(C<T>);
+  if (!t->Md) {
+    HFMM_TRY(tree_alloc(t, &t->Md, csz * t->total_cells * P));
+    HFMM_TRY(tree_alloc(t, &t->Ld, csz * t->total_cells * P));
+    HFMM_TRY(tree_alloc(t, &t->phis_d, csz * t->n_pts));
+    HFMM_CUDA_TRY(cudaMemsetAsync(t->Md, 0, csz * t->total_cells * P, s));
+    HFMM_CUDA_TRY(cudaMemsetAsync(t->Ld, 0, csz * t->total_cells * P, s));
+  }
+  FmmDev<T> d = make_dev<T>(t);
+  const int nleaf = 1 << (3 * L);
+  const int64_t PP = (int64_t)P * P;
+  const int th = threads_for(P);
+  const C<T>* m2m = ops_of<T>(t, t->op_m2m, t->op_m2m32);
+  const C<T>* l2l = ops_of<T>(t, t->op_l2l, t->op_l2l32);
+  const C<T>* m2l = ops_of<T>(t, t->op_m2l, t->op_m2l32);
+  const C<T>* m2m_d = ops_of<T>(t, t->op_m2m_d, t->op_m2m_d32);
+  const C<T>* l2l_d = ops_of<T>(t, t->op_l2l_d, t->op_l2l_d32);
+  const C<T>* m2l_d = ops_of<T>(t, t->op_m2l_d, t->op_m2l_d32);
+  C<T>* Md = reinterpret_cast<C<T>*>(t->Md);
+  C<T>* Ld = reinterpret_cast<C<T>*>(t->Ld);
+  C<T>* phd = reinterpret_cast<C<T>*>(t->phis_d);
+  const int chunk = 32;
+  size_t sm_p2m = (size_t)chunk * P * csz;
+  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
+  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, true>, sm_p2m));
+  k_p2m<T, false><<<nleaf, 64, sm_p2m, s>>>(d, d.M, t->level_off[L], src_set, chunk, mkc<T>(1, 0));
+  k_p2m<T, true><<<nleaf, 64, sm_p2m, s>>>(d, Md, t->level_off[L], src_set, chunk, mkc<T>(1, 0));
+  size_t sm8 = 8 * (size_t)P * csz;
+  HFMM_TRY(set_smem<T>((const void*)k_m2m<T>, sm8));
+  for (int l = L - 1; l >= 2; --l) {
+    const int64_t o = (int64_t)l * 8 * PP;
+    k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], d.M, d.M, m2m + o,
+                                            src_set, 0);
+    k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], Md, Md, m2m + o,
+                                            src_set, 0);
+    k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], d.M, Md, m2m_d + o,
+                                            src_set, 1);
+  }
+  int n1 = 0, n2 = 0, n3 = 0;
+  HFMM_TRY(m2l_stage<T>(t, d, m2l, src_set, tgt_set, 0, s, &n1));  // L
+  FmmDev<T> dd = d;
+  dd.M = Md;
+  dd.Lc = Ld;
+  HFMM_TRY(m2l_stage<T>(t, dd, m2l, src_set, tgt_set, 0, s, &n2));  // dL = T dM
+  FmmDev<T> dx = d;
+  dx.Lc = Ld;
+  HFMM_TRY(m2l_stage<T>(t, dx, m2l_d, src_set, tgt_set, 1, s, &n3));  // dL += dT M
+  size_t sm1 = (size_t)P * csz;
+  for (int l = 2; l < L; ++l) {
+    const int64_t o = (int64_t)l * 8 * PP;
+    k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], d.Lc, d.Lc, l2l + o,
+                                                  tgt_set);
+    k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], Ld, Ld, l2l + o,
+                                                  tgt_set);
+    k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], d.Lc, Ld,
+                                                  l2l_d + o, tgt_set);
+  }
+  k_l2p_dk<T><<<nleaf, 64, 2 * sm1, s>>>(d, d.Lc, Ld, phd, t->level_off[L], tgt_set);
+  FmmDev<T> dp = d;
+  dp.phis = phd;
+  HFMM_TRY(p2p_stage<T, 2>(t, dp, src_set, tgt_set, t->dsigma_vol, t->dsigma_bnd, s));
+  count_launches(4 + 6 * (L > 2 ? L - 2 : 0) + n1 + n2 + n3);
+  return hfmm_last_launch();
+}
+
 template <typename T>
 int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   FmmDev<T> d = make_dev<T>(t);
@@ -1281,14 +1581,15 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   const C<T>* m2l = reinterpret_cast<const C<T>*>(sizeof(T) == 4 ? (void*)t->op_m2l32 : (void*)t->op_m2l);
   const int64_t PP = (int64_t)P * P;
   const int th = threads_for(P);
+  (void)nleaf;
 
   StageTimer& tm = t->timer;
   // P2M
   const int chunk = 32;
   size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
-  HFMM_TRY(set_smem<T>((const void*)k_p2m<T>, sm_p2m));
+  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
   tm.begin(HFMM_STAGE_P2M, s);
-  k_p2m<T><<<nleaf, 64, sm_p2m, s>>>(d, t->level_off[L], src_set, chunk);
+  k_p2m<T, false><<<nleaf, 64, sm_p2m, s>>>(d, d.M, t->level_off[L], src_set, chunk, mkc<T>(1, 0));
   tm.end(1, s);
   count_launches(1);
   // M2M, levels L-1 .. 2
@@ -1297,63 +1598,33 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   if (L > 2) {
     tm.begin(HFMM_STAGE_M2M, s);
     for (int l = L - 1; l >= 2; --l)
-      k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1],
-                                              m2m + (int64_t)l * 8 * PP, src_set);
+      k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], d.M, d.M,
+                                              m2m + (int64_t)l * 8 * PP, src_set, 0);
     tm.end(L - 2, s);
     count_launches(L - 2);
   }
-  // M2L, levels 2 .. L: tiled kernel in one launch when the operator fits in
-  // shared memory, else one launch per level of the per-cell kernel
-  size_t sm1 = (size_t)P * sizeof(C<T>);
+  // M2L, levels 2 .. L
   tm.begin(HFMM_STAGE_M2L, s);
   int nm2l = 0;
-  const bool tiled = (sizeof(T) == 4 && P <= 81) || (sizeof(T) == 8 && P <= 64);
-  const bool tma = tiled && (P % 2 == 0);  // rows are 16-byte multiples; pairs of columns per load
-  if (tma) {
-    int st;
-    if (t->m2l_tc == 32)
-      st = launch_m2l_tma<T, 4>(t, d, m2l, src_set, tgt_set, s);
-    else
-      st = launch_m2l_tma<T, 2>(t, d, m2l, src_set, tgt_set, s);
-    HFMM_TRY(st);
-    nm2l = 0;  // counted by the launcher
-  } else if (tiled) {
-    int st;
-    if (t->m2l_tc == 32)  // tiles hold up to 32 cells: 8 column groups x 4
-      st = launch_m2l_tiled<T, 4>(t, d, m2l, t->level_off_dev, src_set, tgt_set, s);
-    else                  // 16 cells: 8 x 2
-      st = launch_m2l_tiled<T, 2>(t, d, m2l, t->level_off_dev, src_set, tgt_set, s);
-    HFMM_TRY(st);
-    nm2l = 1;
-  } else {
-    for (int l = 2; l <= L; ++l)
-      k_m2l<T><<<1 << (3 * l), th, sm1, s>>>(d, l, t->level_off[l], m2l + (int64_t)l * t->box_cells * PP,
-                                              t->m2l_off, t->m2l_box_index, t->m2l_count, src_set,
-                                              tgt_set);
-    nm2l = L - 1;
-  }
+  HFMM_TRY(m2l_stage<T>(t, d, m2l, src_set, tgt_set, 0, s, &nm2l));
   tm.end(nm2l > 0 ? nm2l : 1, s, tm.on ? m2l_work(t, src_set, tgt_set) : 0.0);
   count_launches(nm2l);
   // L2L, levels 2 .. L-1 into their children
+  size_t sm1 = (size_t)P * sizeof(C<T>);
   if (L > 2) {
     tm.begin(HFMM_STAGE_L2L, s);
     for (int l = 2; l < L; ++l)
-      k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1],
+      k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], d.Lc, d.Lc,
                                                     l2l + (int64_t)l * 8 * PP, tgt_set);
     tm.end(L - 2, s);
     count_launches(L - 2);
   }
   // L2P then P2P (adds)
   tm.begin(HFMM_STAGE_L2P, s);
-  k_l2p<T><<<nleaf, 64, sm1, s>>>(d, t->level_off[L], tgt_set);
+  k_l2p<T><<<nleaf, 64, sm1, s>>>(d, t->level_off[L], tgt_set, mkc<T>(0, d.k));
   tm.end(1, s);
   tm.begin(HFMM_STAGE_P2P, s);
-  if (t->near_count <= 128)
-    k_p2p_v2<T, (sizeof(T) == 4 ? 1536 : 768)><<<nleaf, 256, 0, s>>>(
-        d, t->near_off, t->near_count, src_set, tgt_set, t->sigma_vol, t->sigma_bnd);
-  else
-    k_p2p<T><<<nleaf, 128, 0, s>>>(d, t->near_off, t->near_count, src_set, tgt_set, t->sigma_vol,
-                                    t->sigma_bnd);
+  HFMM_TRY(p2p_stage<T, 0>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));
   tm.end(1, s, tm.on ? p2p_work(t, src_set, tgt_set) : 0.0);
   count_launches(2);
   return hfmm_last_launch();
@@ -1392,15 +1663,30 @@ int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   return core_impl<double>(t, src_set, tgt_set, s);
 }
 
+int fmm_core_adjoint(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
+  if (t->precision == HFMM_FP32) return core_adjoint_impl<float>(t, src_set, tgt_set, s);
+  return core_adjoint_impl<double>(t, src_set, tgt_set, s);
+}
+
+int fmm_core_dk(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
+  if (t->precision == HFMM_FP32) return core_dk_impl<float>(t, src_set, tgt_set, s);
+  return core_dk_impl<double>(t, src_set, tgt_set, s);
+}
+
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cudaStream_t s) {
+  return fmm_scatter_from(t, t->phis, tgt_set, phi_vol, phi_bnd, s);
+}
+
+int fmm_scatter_from(fmm_tree* t, const void* sorted, int tgt_set, double2* phi_vol, double2* phi_bnd,
+                     cudaStream_t s) {
   unsigned g = ceil_div(t->n_pts, 256);
   t->timer.begin(HFMM_STAGE_GATHER, s);
   if (t->precision == HFMM_FP32)
     k_scatter<float><<<g, 256, 0, s>>>(t->pos_of, t->n_vol, t->n_bnd, tgt_set,
-                                       reinterpret_cast<const float2*>(t->phis), phi_vol, phi_bnd);
+                                       reinterpret_cast<const float2*>(sorted), phi_vol, phi_bnd);
   else
     k_scatter<double><<<g, 256, 0, s>>>(t->pos_of, t->n_vol, t->n_bnd, tgt_set,
-                                        reinterpret_cast<const double2*>(t->phis), phi_vol, phi_bnd);
+                                        reinterpret_cast<const double2*>(sorted), phi_vol, phi_bnd);
   t->timer.end(1, s);
   count_launches(1);
   return hfmm_last_launch();

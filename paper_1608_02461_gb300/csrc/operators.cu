@@ -91,6 +91,7 @@ struct OpSet {
   int nops;     // operators per level
   int mode;     // 0: M2L offsets from `off`, 1: M2M child->parent, 2: L2L parent->child
   const int* off;  // packed offsets per slot (mode 0)
+  int deriv;    // 1: d/dk of the operator (z_l(k|t|) -> |t| z_l'(k|t|))
 };
 
 __global__ void k_translation(int p, double k, int lmin, OpSet set, const double* gt, double2* out) {
@@ -125,12 +126,26 @@ __global__ void k_translation(int p, double k, int lmin, OpSet set, const double
     geo[2] = st;
     geo[3] = cp;
     geo[4] = sp;
-    double jl[2 * HFMM_MAX_P], yl[2 * HFMM_MAX_P];
-    sph_bessel_j<double>(k * r, lmax, jl);
-    if (set.kind == 1) sph_bessel_y(k * r, lmax, yl);
+    double jl[2 * HFMM_MAX_P + 1], yl[2 * HFMM_MAX_P + 1];
+    sph_bessel_j<double>(k * r, lmax + 1, jl);
+    if (set.kind == 1) sph_bessel_y(k * r, lmax + 1, yl);
     for (int l = 0; l < lmax; ++l) {
-      zr[l] = jl[l];
-      zi[l] = set.kind == 1 ? yl[l] : 0.0;
+      double a = jl[l], b = set.kind == 1 ? yl[l] : 0.0;
+      if (set.deriv) {
+        // d/dk z_l(k r) = r z_l'(k r); z_0' = -z_1, z_l' = z_{l-1} - (l+1)/x z_l
+        double x = k * r;
+        if (l == 0) {
+          a = -jl[1];
+          b = set.kind == 1 ? -yl[1] : 0.0;
+        } else {
+          a = jl[l - 1] - (l + 1) / x * jl[l];
+          b = set.kind == 1 ? yl[l - 1] - (l + 1) / x * yl[l] : 0.0;
+        }
+        a *= r;
+        b *= r;
+      }
+      zr[l] = a;
+      zi[l] = b;
     }
     legendre_bar<double>(ct, st, lmax, pl);
   }
@@ -210,13 +225,13 @@ int build_operators(fmm_tree* t, cudaStream_t s) {
   HFMM_CUDA_TRY(cudaMemsetAsync(t->op_m2l, 0, sizeof(double2) * (L + 1) * t->box_cells * PP, s));
 
   if (L >= 3) {
-    OpSet m2m{0, 8, 1, nullptr}, l2l{0, 8, 2, nullptr};
+    OpSet m2m{0, 8, 1, nullptr, 0}, l2l{0, 8, 2, nullptr, 0};
     dim3 g(8, L - 2);  // levels 2..L-1
     k_translation<<<g, 256, 0, s>>>(p, t->k, 2, m2m, gt, t->op_m2m + 2 * 8 * PP);
     k_translation<<<g, 256, 0, s>>>(p, t->k, 2, l2l, gt, t->op_l2l + 2 * 8 * PP);
   }
   {
-    OpSet m2l{1, (int)t->box_cells, 0, t->m2l_slot_off};
+    OpSet m2l{1, (int)t->box_cells, 0, t->m2l_slot_off, 0};
     dim3 g((unsigned)t->box_cells, L - 1);  // levels 2..L
     k_translation<<<g, 256, 0, s>>>(p, t->k, 2, m2l, gt, t->op_m2l + 2 * t->box_cells * PP);
   }
@@ -231,6 +246,109 @@ int build_operators(fmm_tree* t, cudaStream_t s) {
     k_to_float<<<ceil_div(n2, 256), 256, 0, s>>>(t->op_m2l, t->op_m2l32, n2);
     HFMM_TRY(hfmm_last_launch());
   }
-  cudaFreeAsync(gt, s);
+  t->gaunt = gt;  // kept for the derivative operators (freed with the handle)
+  return hfmm_last_launch();
+}
+
+namespace {
+
+// slot of the negated offset: neg[slot(v)] = slot(-v) (the M2L offset set is
+// symmetric); one thread per slot
+__global__ void k_slot_neg(int nslots, const int* slot_off, int* neg) {
+  int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= nslots) return;
+  int o = slot_off[sl];
+  int dx = (o & 255) - 128, dy = ((o >> 8) & 255) - 128, dz = ((o >> 16) & 255) - 128;
+  int want = (-dx + 128) | ((-dy + 128) << 8) | ((-dz + 128) << 16);
+  int r = -1;
+  for (int q = 0; q < nslots; ++q)
+    if (slot_off[q] == want) r = q;
+  neg[sl] = r;
+}
+
+// Hermitian adjoints.  Column-major (M2M/L2L): out(a', a) = conj(in(a, a'));
+// row-major M2L with slot map: out[slot](a', a) = conj(in[neg[slot]](a, a')).
+__global__ void k_adjoint_colmajor(const double2* in, double2* out, int P, int64_t nmat) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t PP = (int64_t)P * P;
+  if (e >= nmat * PP) return;
+  int64_t m = e / PP, r = e % PP;
+  int a = (int)(r / P), ap = (int)(r % P);  // element (a', a) at a*P + a'
+  double2 v = in[m * PP + (int64_t)ap * P + a];
+  out[e] = make_double2(v.x, -v.y);
+}
+__global__ void k_adjoint_m2l(const double2* in, double2* out, int P, int nslots, int levels,
+                              const int* neg) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t PP = (int64_t)P * P;
+  if (e >= (int64_t)levels * nslots * PP) return;
+  int64_t m = e / PP, r = e % PP;
+  int level = (int)(m / nslots), sl = (int)(m % nslots);
+  int ap = (int)(r / P), a = (int)(r % P);  // row-major element (a', a)
+  int src = neg[sl];
+  double2 v = src >= 0 ? in[((int64_t)level * nslots + src) * PP + (int64_t)a * P + ap] : make_double2(0, 0);
+  out[e] = make_double2(v.x, -v.y);
+}
+
+}  // namespace
+
+// d/dk operators (tangent mode) and Hermitian adjoint operators (adjoint
+// mode), built on first use of those modes
+int build_operators_deriv(fmm_tree* t, cudaStream_t s) {
+  if (t->op_m2l_d) return HFMM_OK;
+  const int p = t->p, P = t->P, L = t->L;
+  const int64_t PP = (int64_t)P * P;
+  const int64_t n1 = (int64_t)(L + 1) * 8 * PP, n2 = (int64_t)(L + 1) * t->box_cells * PP;
+  HFMM_TRY(tree_alloc_t(t, &t->op_m2m_d, n1));
+  HFMM_TRY(tree_alloc_t(t, &t->op_l2l_d, n1));
+  HFMM_TRY(tree_alloc_t(t, &t->op_m2l_d, n2));
+  HFMM_CUDA_TRY(cudaMemsetAsync(t->op_m2m_d, 0, sizeof(double2) * n1, s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(t->op_l2l_d, 0, sizeof(double2) * n1, s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(t->op_m2l_d, 0, sizeof(double2) * n2, s));
+  if (L >= 3) {
+    OpSet m2m{0, 8, 1, nullptr, 1}, l2l{0, 8, 2, nullptr, 1};
+    dim3 g(8, L - 2);
+    k_translation<<<g, 256, 0, s>>>(p, t->k, 2, m2m, t->gaunt, t->op_m2m_d + 2 * 8 * PP);
+    k_translation<<<g, 256, 0, s>>>(p, t->k, 2, l2l, t->gaunt, t->op_l2l_d + 2 * 8 * PP);
+  }
+  OpSet m2l{1, (int)t->box_cells, 0, t->m2l_slot_off, 1};
+  k_translation<<<dim3((unsigned)t->box_cells, L - 1), 256, 0, s>>>(p, t->k, 2, m2l, t->gaunt,
+                                                                    t->op_m2l_d + 2 * t->box_cells * PP);
+  HFMM_TRY(hfmm_last_launch());
+  if (t->precision == HFMM_FP32) {
+    HFMM_TRY(tree_alloc_t(t, &t->op_m2m_d32, n1));
+    HFMM_TRY(tree_alloc_t(t, &t->op_l2l_d32, n1));
+    HFMM_TRY(tree_alloc_t(t, &t->op_m2l_d32, n2));
+    k_to_float<<<ceil_div(n1, 256), 256, 0, s>>>(t->op_m2m_d, t->op_m2m_d32, n1);
+    k_to_float<<<ceil_div(n1, 256), 256, 0, s>>>(t->op_l2l_d, t->op_l2l_d32, n1);
+    k_to_float<<<ceil_div(n2, 256), 256, 0, s>>>(t->op_m2l_d, t->op_m2l_d32, n2);
+  }
+  return hfmm_last_launch();
+}
+
+int build_operators_adjoint(fmm_tree* t, cudaStream_t s) {
+  if (t->op_m2l_h) return HFMM_OK;
+  const int P = t->P, L = t->L;
+  const int64_t PP = (int64_t)P * P;
+  const int64_t n1 = (int64_t)(L + 1) * 8 * PP, n2 = (int64_t)(L + 1) * t->box_cells * PP;
+  HFMM_TRY(tree_alloc_t(t, &t->m2l_slot_neg, t->box_cells));
+  k_slot_neg<<<ceil_div(t->box_cells, 128), 128, 0, s>>>((int)t->box_cells, t->m2l_slot_off,
+                                                         t->m2l_slot_neg);
+  HFMM_TRY(tree_alloc_t(t, &t->op_m2m_h, n1));
+  HFMM_TRY(tree_alloc_t(t, &t->op_l2l_h, n1));
+  HFMM_TRY(tree_alloc_t(t, &t->op_m2l_h, n2));
+  k_adjoint_colmajor<<<ceil_div(n1, 256), 256, 0, s>>>(t->op_m2m, t->op_m2m_h, P, (L + 1) * 8);
+  k_adjoint_colmajor<<<ceil_div(n1, 256), 256, 0, s>>>(t->op_l2l, t->op_l2l_h, P, (L + 1) * 8);
+  k_adjoint_m2l<<<ceil_div(n2, 256), 256, 0, s>>>(t->op_m2l, t->op_m2l_h, P, (int)t->box_cells, L + 1,
+                                                  t->m2l_slot_neg);
+  HFMM_TRY(hfmm_last_launch());
+  if (t->precision == HFMM_FP32) {
+    HFMM_TRY(tree_alloc_t(t, &t->op_m2m_h32, n1));
+    HFMM_TRY(tree_alloc_t(t, &t->op_l2l_h32, n1));
+    HFMM_TRY(tree_alloc_t(t, &t->op_m2l_h32, n2));
+    k_to_float<<<ceil_div(n1, 256), 256, 0, s>>>(t->op_m2m_h, t->op_m2m_h32, n1);
+    k_to_float<<<ceil_div(n1, 256), 256, 0, s>>>(t->op_l2l_h, t->op_l2l_h32, n1);
+    k_to_float<<<ceil_div(n2, 256), 256, 0, s>>>(t->op_m2l_h, t->op_m2l_h32, n2);
+  }
   return hfmm_last_launch();
 }

@@ -366,46 +366,84 @@ __device__ double2 radial_panel(double a) {
 // s_vol = 6 (h/2) int_{face} Iv(k R) / (4 pi R) dA,  R = |(h/2, u, v)|
 // s_bnd = 4 (h/2) int_{edge} Ip(k R) / (4 pi R) du,  R = |(h/2, u)|
 // (pyramids / triangles with apex at the singular point, radial part exact)
+// and their k-derivatives, from d/dk Iv(k R) = R Iv'(k R), Iv'(a) = i int_0^1 s^2 e^{ias} ds,
+// Ip'(a) = i int_0^1 s e^{ias} ds = i Iv(a).
+__device__ double2 radial_vol_d(double a) {  // i int_0^1 s^2 e^{ias} ds
+  double2 v;
+  if (a < 1.0) {  // sum_m (i a)^m / (m! (m + 3))
+    double2 s = make_double2(0, 0), t = make_double2(1, 0);
+    for (int m = 0; m < 40; ++m) {
+      s.x += t.x / (m + 3);
+      s.y += t.y / (m + 3);
+      double2 tn = make_double2(-t.y * a / (m + 1), t.x * a / (m + 1));
+      t = tn;
+    }
+    v = s;
+  } else {  // e^{ia}/(ia) - (2/(ia)) Iv(a)
+    double sa, ca;
+    sincos(a, &sa, &ca);
+    double2 I = radial_vol(a);
+    // 1/(ia) = -i/a
+    double2 e = make_double2(sa / a, -ca / a);
+    double2 t2 = make_double2(2.0 * I.y / a, -2.0 * I.x / a);  // (2/(ia)) I = -2i I / a
+    v = make_double2(e.x - t2.x, e.y - t2.y);
+  }
+  return make_double2(-v.y, v.x);  // times i
+}
+
 __global__ void k_self_terms(double h, double k, double2* out) {
   constexpr int NQ = 32;
   __shared__ double xg[NQ], wg[NQ];
-  __shared__ double2 red[256];
+  __shared__ double2 red[256], red2[256];
   if (threadIdx.x == 0) gauss_legendre(NQ, xg, wg);
   __syncthreads();
   const double hh = 0.5 * h;
   const double inv4pi = 0.25 / M_PI;
-  double2 acc = make_double2(0, 0);
+  double2 acc = make_double2(0, 0), accd = make_double2(0, 0);
   for (int q = threadIdx.x; q < NQ * NQ; q += blockDim.x) {
     int i = q % NQ, j = q / NQ;
     double u = hh * xg[i], v = hh * xg[j];
     double R = sqrt(hh * hh + u * u + v * v);
     double2 I = radial_vol(k * R);
-    double wt = hh * wg[i] * hh * wg[j] * inv4pi / R;
-    acc.x += wt * I.x;
-    acc.y += wt * I.y;
+    double2 Id = radial_vol_d(k * R);
+    double wt = hh * wg[i] * hh * wg[j] * inv4pi;
+    acc.x += wt / R * I.x;
+    acc.y += wt / R * I.y;
+    accd.x += wt * Id.x;
+    accd.y += wt * Id.y;
   }
   red[threadIdx.x] = acc;
+  red2[threadIdx.x] = accd;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
       red[threadIdx.x].x += red[threadIdx.x + s].x;
       red[threadIdx.x].y += red[threadIdx.x + s].y;
+      red2[threadIdx.x].x += red2[threadIdx.x + s].x;
+      red2[threadIdx.x].y += red2[threadIdx.x + s].y;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = make_double2(6 * hh * red[0].x, 6 * hh * red[0].y);
+  if (threadIdx.x == 0) {
+    out[0] = make_double2(6 * hh * red[0].x, 6 * hh * red[0].y);
+    out[2] = make_double2(6 * hh * red2[0].x, 6 * hh * red2[0].y);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double2 a2 = make_double2(0, 0);
+    double2 a2 = make_double2(0, 0), a2d = make_double2(0, 0);
     for (int i = 0; i < NQ; ++i) {
       double u = hh * xg[i];
       double R = sqrt(hh * hh + u * u);
       double2 I = radial_panel(k * R);
-      double wt = hh * wg[i] * inv4pi / R;
-      a2.x += wt * I.x;
-      a2.y += wt * I.y;
+      double2 Iv = radial_vol(k * R);  // Ip'(a) = i Iv(a)
+      double wt = hh * wg[i] * inv4pi;
+      a2.x += wt / R * I.x;
+      a2.y += wt / R * I.y;
+      a2d.x += wt * (-Iv.y);
+      a2d.y += wt * Iv.x;
     }
     out[1] = make_double2(4 * hh * a2.x, 4 * hh * a2.y);
+    out[3] = make_double2(4 * hh * a2d.x, 4 * hh * a2d.y);
   }
 }
 
@@ -547,10 +585,10 @@ int build_self_terms(fmm_tree* t, cudaStream_t s) {
     return HFMM_OK;
   }
   double2* d = nullptr;
-  HFMM_CUDA_TRY(cudaMallocAsync((void**)&d, sizeof(double2) * 2, s));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&d, sizeof(double2) * 4, s));
   k_self_terms<<<1, 256, 0, s>>>(t->h, t->k, d);
   HFMM_TRY(hfmm_last_launch());
-  double2 hs[2];
+  double2 hs[4];
   HFMM_CUDA_TRY(cudaMemcpyAsync(hs, d, sizeof(hs), cudaMemcpyDeviceToHost, s));
   HFMM_CUDA_TRY(cudaStreamSynchronize(s));
   cudaFreeAsync(d, s);
@@ -559,6 +597,8 @@ int build_self_terms(fmm_tree* t, cudaStream_t s) {
   const double h3 = t->h * t->h * t->h, h2 = t->h * t->h;
   t->sigma_vol = make_double2(hs[0].x / h3, hs[0].y / h3);
   t->sigma_bnd = make_double2(hs[1].x / h2, hs[1].y / h2);
+  t->dsigma_vol = make_double2(hs[2].x / h3, hs[2].y / h3);
+  t->dsigma_bnd = make_double2(hs[3].x / h2, hs[3].y / h2);
   return HFMM_OK;
 }
 

@@ -135,6 +135,20 @@ struct fmm_tree {
   float2* op_l2l32 = nullptr;
   float2* op_m2l32 = nullptr;
   int64_t box_cells = 0;        // distinct M2L offsets = operator slots per level
+  double* gaunt = nullptr;      // Gaunt integrals [P][P][2p-1] (operator builds)
+  // d/dk operators (tangent mode) and Hermitian adjoints (adjoint mode): same
+  // layouts as the forward ones, built on first use
+  double2 *op_m2m_d = nullptr, *op_l2l_d = nullptr, *op_m2l_d = nullptr;
+  float2 *op_m2m_d32 = nullptr, *op_l2l_d32 = nullptr, *op_m2l_d32 = nullptr;
+  double2 *op_m2m_h = nullptr, *op_l2l_h = nullptr, *op_m2l_h = nullptr;
+  float2 *op_m2m_h32 = nullptr, *op_l2l_h32 = nullptr, *op_m2l_h32 = nullptr;
+  int* m2l_slot_neg = nullptr;  // slot of the negated offset
+  // tangent-mode work arrays (precision T), allocated on first use
+  void* Md = nullptr;           // dM/dk [total_cells][P]
+  void* Ld = nullptr;           // dL/dk [total_cells][P]
+  void* phis_d = nullptr;       // dphi/dk sorted [n_pts]
+  // singular self coefficients' k-derivatives per unit weight
+  double2 dsigma_vol = {0, 0}, dsigma_bnd = {0, 0};
 
   // ---- singular self coefficients per unit weight
   double2 sigma_vol = {0, 0};   // s_Omega / h^3
@@ -183,14 +197,22 @@ double m2l_work(const fmm_tree* t, int src_set, int tgt_set);
 
 // operators.cu
 int build_operators(fmm_tree* t, cudaStream_t s);
+int build_operators_deriv(fmm_tree* t, cudaStream_t s);
+int build_operators_adjoint(fmm_tree* t, cudaStream_t s);
 
 // fmm.cu: sorted-weight gather, FMM core over the sorted vectors, scatter
 int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol,
                const double2* q_bnd, double scale_bnd, cudaStream_t s);
 int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
+// adjoint pass: weights in qs on the points of tgt_set, result in phis on src_set
+int fmm_core_adjoint(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
+// tangent pass: d(phi)/dk into phis for the weights in qs
+int fmm_core_dk(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
 // HFMM_ERR_TIMEOUT (or 0) recorded by a kernel's bounded wait; synchronises s
 int fmm_device_error(cudaStream_t s, bool clear);
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cudaStream_t s);
+int fmm_scatter_from(fmm_tree* t, const void* sorted, int tgt_set, double2* phi_vol, double2* phi_bnd,
+                     cudaStream_t s);
 
 // krylov.cu
 int fdm_apply_dev(int n, double h, double k, const double2* u, double2* out, cudaStream_t s);

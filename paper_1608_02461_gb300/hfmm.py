@@ -25,6 +25,8 @@ HFMM_FP32 = 1
 SET_VOL = 1
 SET_BND = 2
 FWD = 0
+ADJ = 1
+DK = 2
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhfmm.so")
 
@@ -187,19 +189,22 @@ class Tree:
             pass
 
     def apply(self, q_vol=None, q_bnd=None, src=SET_VOL | SET_BND, tgt=SET_VOL | SET_BND,
-              phi_vol=None, phi_bnd=None, stream=None):
+              phi_vol=None, phi_bnd=None, mode=FWD, stream=None):
+        """fmm_apply.  FWD/DK: q on `src`, phi on `tgt`; ADJ: q on `tgt`,
+        phi on `src` (conjugate transpose)."""
         torch = _torch()
         dev = (q_vol if q_vol is not None else q_bnd).device
-        if (tgt & SET_VOL) and phi_vol is None:
+        out_set = src if mode == ADJ else tgt
+        if (out_set & SET_VOL) and phi_vol is None:
             phi_vol = torch.empty(self.n_vol, dtype=torch.complex128, device=dev)
-        if (tgt & SET_BND) and phi_bnd is None:
+        if (out_set & SET_BND) and phi_bnd is None:
             phi_bnd = torch.empty(self.n_bnd, dtype=torch.complex128, device=dev)
         if q_vol is not None:
             _dev_c128(q_vol, self.n_vol, "q_vol")
         if q_bnd is not None:
             _dev_c128(q_bnd, self.n_bnd, "q_bnd")
         st = lib().fmm_apply(self._h, src, tgt, _ptr(q_vol), _ptr(q_bnd), _ptr(phi_vol),
-                             _ptr(phi_bnd), FWD, _stream_ptr(stream))
+                             _ptr(phi_bnd), mode, _stream_ptr(stream))
         _check(st, "fmm_apply")
         return phi_vol, phi_bnd
 
