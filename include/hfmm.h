@@ -229,6 +229,31 @@ int hfmm_fdm_apply(fmm_tree* tree, const void* d_u, void* d_out, void* stream);
 int gmres_solve(fmm_tree* tree, const void* d_b, void* d_x,
                 const hfmm_gmres_params* gp, hfmm_gmres_info* info, void* stream);
 
+/*
+ * gmres_solve_batched -- many independent solves of gmres_solve (Sec. 3-4,
+ * Sec. 6), e.g. right-hand sides and wavenumbers of uneven grid sizes, one
+ * handle per solve.  The solves run concurrently: worker threads drive them
+ * on their own streams so that their kernels overlap on the GPU.  Work on
+ * `stream` before the call is ordered before the batch, and work queued on
+ * `stream` after it waits for the whole batch.
+ *   trees[count], d_b[count], d_x[count]   as in gmres_solve; the handles
+ *                                          must be distinct
+ *   infos                                  optional host array [count]
+ * Returns the first hard error, else HFMM_ERR_NOT_CONVERGED if any solve did
+ * not converge, else HFMM_OK.  Blocks the calling thread until done.
+ */
+int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_x, int count,
+                        const hfmm_gmres_params* gp, hfmm_gmres_info* infos, void* stream);
+
+/*
+ * fmm_autotune -- times the M2L kernel variants (two-stage block pipeline,
+ * warp-specialised three-stage pipeline) and the split of the per-tile
+ * offset lists (grid filled to 1, 2, 4 or 8 x 152 blocks) on the FMM passes
+ * of the preconditioner and on the full apply, and keeps the fastest per pass
+ * in the handle.  Results are unchanged by the choice (deterministic sums).
+ */
+int fmm_autotune(fmm_tree* tree, void* stream);
+
 /* Sizes and counters of a built tree.  Waits for the handle's pending
  * timing events (host blocks until they complete). */
 int fmm_get_stats(const fmm_tree* tree, hfmm_stats* stats);

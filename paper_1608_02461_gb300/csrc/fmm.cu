@@ -860,14 +860,17 @@ int launch_m2l_tma_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_
   const int ci = mi * 3 + (src_set - 1);
   size_t sm = 1024 + (2 * (size_t)P * P + 2 * (size_t)TC * (P + 2)) * sizeof(C<T>);
   // split the offset lists so that the grid fills the GPU a few times over
-  int nsplit = (4 * 152 + nt - 1) / nt;
+  const int tci = mi * 3 + (src_set - 1);
+  const int variant = t->tuned_variant[tci] >= 0 ? t->tuned_variant[tci] : t->m2l_variant;
+  const int fill = t->tuned_variant[tci] >= 0 ? t->tuned_fill[tci] : t->m2l_fill;
+  int nsplit = (fill * 152 + nt - 1) / nt;
   if (nsplit > t->m2l_part_max) nsplit = t->m2l_part_max;
   if (nsplit < 1) nsplit = 1;
   C<T>* part = nsplit > 1 ? reinterpret_cast<C<T>*>(t->m2l_part) : nullptr;
   const int64_t pstride = t->total_cells * (int64_t)P;
   constexpr int NSTG = 3;
   size_t smw = 1024 + (NSTG * (size_t)P * P + NSTG * (size_t)TC * (P + 2)) * sizeof(C<T>);
-  if (t->m2l_variant == 1 && smw <= 200 * 1024 && (RT * 8) % 32 == 0) {
+  if (variant == 1 && smw <= 200 * 1024 && (RT * 8) % 32 == 0) {
     HFMM_TRY(set_smem<T>((const void*)k_m2l_ws<T, R, CM, RT, NSTG>, smw));
     k_m2l_ws<T, R, CM, RT, NSTG><<<dim3(nt, nsplit), RT * 8 + 32, smw, s>>>(
         d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev, ops, t->box_cells, t->m2l_off,

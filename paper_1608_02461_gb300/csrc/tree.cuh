@@ -126,6 +126,11 @@ struct fmm_tree {
   void* m2l_part = nullptr;     // [m2l_part_max][total_cells][P] split-offset partial sums
   int m2l_part_max = 1;
   int m2l_variant = 1;          // 1: warp-specialised pipeline, 0: two-stage block pipeline
+  int m2l_fill = 4;             // split offset lists until the grid holds fill x 152 blocks
+  // autotuned (variant, fill) per (target mask, source mask) pair, index 3 (tm-1) + (sm-1);
+  // variant -1: not tuned (use the defaults above)
+  int tuned_variant[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+  int tuned_fill[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 
   // ---- operators (FP64 master copy; FP32 copy for the FP32 form)
   double2* op_m2m = nullptr;    // [L+1][8][P][P]   row a' (out), column a (in)

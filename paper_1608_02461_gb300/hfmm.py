@@ -83,6 +83,11 @@ SIGNATURES = {
                                    ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
     "fmm_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hfmm_stats)]),
     "fmm_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gmres_solve_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                           ctypes.POINTER(hfmm_gmres_params),
+                                           ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
+    "fmm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hfmm_direct_sum_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                                ctypes.c_void_p, ctypes.c_void_p]),
@@ -255,10 +260,40 @@ class Tree:
         return {name: (s.stage_ms[i], s.stage_launches[i], s.stage_work[i])
                 for i, name in enumerate(STAGES)}
 
+    def autotune(self, stream=None):
+        _check(lib().fmm_autotune(self._h, _stream_ptr(stream)), "fmm_autotune")
+
     def stats(self) -> hfmm_stats:
         s = hfmm_stats()
         _check(lib().fmm_get_stats(self._h, ctypes.byref(s)), "fmm_get_stats")
         return s
+
+
+def gmres_solve_batched(trees, bs, xs=None, restart=50, rtol=1e-6, maxit=0, inner_rtol=1e-2,
+                        inner_maxit=20, inner_m=20, history_len=0, stream=None):
+    """Concurrent independent solves (one tree per right-hand side).  Returns
+    (xs, [GmresInfo]); non-convergence is reported in the infos."""
+    torch = _torch()
+    n = len(trees)
+    if len(bs) != n:
+        raise ValueError("one right-hand side per tree")
+    for t, b in zip(trees, bs):
+        _dev_c128(b, t.n_vol, "b")
+    if xs is None:
+        xs = [torch.zeros_like(b) for b in bs]
+    hs = (ctypes.c_void_p * n)(*[t._h.value for t in trees])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    gp = hfmm_gmres_params(restart, rtol, maxit, inner_rtol, inner_maxit, inner_m)
+    hist = [(ctypes.c_double * max(1, history_len))() for _ in range(n)]
+    infos = (hfmm_gmres_info * n)(*[hfmm_gmres_info(0, 0, 0, 0, 0.0, 0.0, hist[i], history_len)
+                                    for i in range(n)])
+    st = lib().gmres_solve_batched(hs, bp, xp, n, ctypes.byref(gp), infos, _stream_ptr(stream))
+    if st not in (HFMM_OK, HFMM_ERR_NOT_CONVERGED):
+        raise HfmmError(st, "gmres_solve_batched")
+    out = [GmresInfo(i.iters, i.restarts, i.inner_iters_total, i.status, i.relres_est, i.relres_true,
+                     list(hist[j][:min(i.iters, history_len)])) for j, i in enumerate(infos)]
+    return xs, out
 
 
 def direct_sum_noalloc(src_xyz, q, tgt_xyz, k, phi, stream=None):

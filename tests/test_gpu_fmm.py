@@ -56,6 +56,9 @@ CASES = [
     (16, 4.0, 4, 32, 0.4),
     (13, 9.0, 6, 16, 0.35),
     (10, 2.5, 5, 8, 0.4),
+    # high k w at the coarse levels (k |t| up to ~50: upward Bessel recurrences)
+    (12, 25.0, 4, 16, 0.4),
+    (12, 25.0, 8, 16, 0.35),
 ]
 
 
