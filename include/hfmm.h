@@ -250,7 +250,9 @@ int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_x, int coun
  * warp-specialised three-stage pipeline) and the split of the per-tile
  * offset lists (grid filled to 1, 2, 4 or 8 x 152 blocks) on the FMM passes
  * of the preconditioner and on the full apply, and keeps the fastest per pass
- * in the handle.  Results are unchanged by the choice (deterministic sums).
+ * in the handle.  The choice changes only the order in which far-field
+ * contributions are summed (rounding-level differences); a handle's results
+ * stay deterministic.
  */
 int fmm_autotune(fmm_tree* tree, void* stream);
 

@@ -7,8 +7,8 @@
 // overlap on the GPU.  The caller's stream is ordered before and after the
 // batch with events.
 //
-// fmm_autotune times the M2L kernel variants (two-stage block pipeline or
-// warp-specialised three-stage pipeline) and the split of the offset lists
+// fmm_autotune times the M2L kernel variants (two-stage block pipeline,
+// warp-specialised three-stage pipeline, pair lists) and the split of the offset lists
 // (grid filled to 1, 2, 4 or 8 times the SM count) on the FMM passes the
 // preconditioner uses, and keeps the fastest per pass in the handle.
 #include <algorithm>
@@ -58,8 +58,9 @@ extern "C" int fmm_autotune(fmm_tree* t, void* stream) {
     const int ci = (tgt - 1) * 3 + (src - 1);
     float best = 1e30f;
     int bv = -1, bf = 0;
-    for (int v = 0; v < 2; ++v)
+    for (int v = 0; v < 3; ++v)
       for (int f : fills) {
+        if (v == 2 && f != fills[0]) continue;  // the pair-list form has no split
         t->tuned_variant[ci] = v;
         t->tuned_fill[ci] = f;
         float ms = 0.f;

@@ -849,6 +849,273 @@ int m2l_valid_lists(fmm_tree* t, int sm, int tm, cudaStream_t s) {
   return hfmm_last_launch();
 }
 
+// ---- pair-list M2L (passes whose targets are the boundary cells)
+//
+// For a boundary-target pass most columns of a 32-cell tile would be empty
+// for most offsets.  Here the valid (target, source) cell pairs are listed
+// once per (target mask, source mask), grouped by (level, operator slot) and
+// multiplied in chunks of 32 pairs that share one operator (bulk copies of
+// the operator and the 32 source rows); each pair's product is a row of a
+// buffer, and each target sums its rows in its own fixed order (deterministic).
+
+// per tile cell: number of valid offsets (pass 1) or the pairs (pass 2)
+__global__ void k_pairs_list(const int4* __restrict__ tiles, const int* __restrict__ cells,
+                             const int* __restrict__ flags, const int64_t* __restrict__ level_off,
+                             const int* __restrict__ m2l_off, const int* __restrict__ m2l_slot, int m2l_count,
+                             int src_set, int* __restrict__ cnt, const int* __restrict__ csr,
+                             int* __restrict__ ptgt, int* __restrict__ psrc, int* __restrict__ pkey,
+                             int nslots) {
+  const int4 tile = tiles[blockIdx.x];
+  const int c = threadIdx.x;
+  if (c >= tile.w) return;
+  const int level = tile.x, b = tile.y;
+  const int cell = cells[tile.z + c];
+  const int64_t off = level_off[level];
+  const int s = 1 << level;
+  int ix, iy, iz;
+  morton_decode((uint64_t)cell, ix, iy, iz);
+  int n = 0;
+  int base = csr ? csr[tile.z + c] : 0;
+  for (int i = 0; i < m2l_count; ++i) {
+    const int o = m2l_off[b * m2l_count + i];
+    int jx = ix + (o & 255) - 128, jy = iy + ((o >> 8) & 255) - 128, jz = iz + ((o >> 16) & 255) - 128;
+    if (jx < 0 || jy < 0 || jz < 0 || jx >= s || jy >= s || jz >= s) continue;
+    int sc = (int)morton_encode(jx, jy, jz);
+    if (!(flags[off + sc] & src_set)) continue;
+    if (csr) {
+      ptgt[base + n] = cell;
+      psrc[base + n] = sc;
+      pkey[base + n] = level * nslots + m2l_slot[b * m2l_count + i];
+    }
+    ++n;
+  }
+  if (!csr) cnt[tile.z + c] = n;
+}
+
+// exclusive scan of n counts (one block)
+__global__ void k_scan_counts(const int* cnt, int n, int* out) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x;
+  const int chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int lo = tid * chunk, hi = min(n, lo + chunk);
+  int sum = 0;
+  for (int i = lo; i < hi; ++i) sum += cnt[i];
+  part[tid] = sum;
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      int v = part[i];
+      part[i] = run;
+      run += v;
+    }
+    out[n] = run;
+  }
+  __syncthreads();
+  int run = part[tid];
+  for (int i = lo; i < hi; ++i) {
+    out[i] = run;
+    run += cnt[i];
+  }
+}
+
+// group pair indices by key with per-group cursors (order inside a group is
+// irrelevant to the result: each pair owns its output row)
+__global__ void k_pairs_group(int64_t npairs, const int* __restrict__ pkey, int* __restrict__ cursor,
+                              int* __restrict__ grouped) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npairs) return;
+  int pos = atomicAdd(&cursor[pkey[p]], 1);
+  grouped[pos] = (int)p;
+}
+__global__ void k_count_keys(int64_t npairs, const int* __restrict__ pkey, int* __restrict__ kcnt) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p < npairs) atomicAdd(&kcnt[pkey[p]], 1);
+}
+// chunks of <= 32 pairs per key (one thread)
+__global__ void k_pairs_chunks(int nkeys, int nslots, const int* __restrict__ kstart, int4* __restrict__ chunks,
+                               int* __restrict__ nchunks) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int n = 0;
+  for (int g = 0; g < nkeys; ++g) {
+    int a = kstart[g], e = kstart[g + 1];
+    for (int st = a; st < e; st += 32) chunks[n++] = make_int4(g / nslots, g % nslots, st, min(32, e - st));
+  }
+  *nchunks = n;
+}
+
+// one block per chunk: buf[pair] = T_slot M[source of pair] for its 32 pairs
+template <typename T, int R, int CM, int RT>
+__global__ void __launch_bounds__(RT * 8) k_m2l_pairs(FmmDev<T> d, const int4* __restrict__ chunks,
+                                                      const int* __restrict__ grouped,
+                                                      const int* __restrict__ psrc,
+                                                      const int64_t* __restrict__ level_off,
+                                                      const C<T>* __restrict__ ops, int64_t box_cells,
+                                                      C<T>* __restrict__ buf) {
+  constexpr int CT = 8, TC = CT * CM;
+  const int P = d.P;
+  const int MS = P + 2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  int* pid = reinterpret_cast<int*>(smem_raw + 16);  // [TC]
+  C<T>* Ts = reinterpret_cast<C<T>*>(smem_raw + 256);
+  C<T>* Ms = Ts + (size_t)P * P;
+  const int4 ch = chunks[blockIdx.x];
+  const int level = ch.x, slot = ch.y, first = ch.z, cnt = ch.w;
+  const int64_t off = level_off[level];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < TC) pid[tid] = tid < cnt ? grouped[first + tid] : -1;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t op_bytes = (uint32_t)((size_t)P * P * sizeof(C<T>));
+  const uint32_t row_bytes = (uint32_t)((size_t)P * sizeof(C<T>));
+  if (warp == 0) {
+    if (lane == 0) mbar_expect_tx(&bar[0], op_bytes + (uint32_t)TC * row_bytes);
+    __syncwarp();
+    if (lane == 0)
+      bulk_copy_g2s(Ts, ops + ((int64_t)level * box_cells + slot) * P * P, op_bytes, &bar[0]);
+    if (lane < TC) {
+      const int p = pid[lane];
+      const C<T>* row = p >= 0 ? d.M + (off + psrc[p]) * P : d.M + off * P;  // any valid row for padding
+      bulk_copy_g2s(Ms + (size_t)lane * MS, row, row_bytes, &bar[0]);
+    }
+  }
+  const bool ok = mbar_wait_bounded(&bar[0], 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      atomicExch(&g_fmm_error, HFMM_ERR_TIMEOUT);
+      mbar_wait_bounded(&bar[0], 0);
+    }
+    __syncthreads();
+    return;
+  }
+  const int r0 = tid / CT, c0 = tid % CT;
+  C<T> acc[R][CM];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = 0; j < CM; ++j) acc[r][j] = mkc<T>(0, 0);
+  m2l_block_product<T, R, CM, RT>(Ts, Ms, P, MS, r0, c0, acc);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int j = 0; j < CM; ++j) {
+      int ap = r0 + r * RT, c = c0 + j * CT;
+      if (ap < P && c < cnt) buf[(int64_t)pid[c] * P + ap] = acc[r][j];
+    }
+}
+
+// L of each tile cell = (L +) sum of its pair rows, in its CSR order
+template <typename T>
+__global__ void k_pairs_reduce(FmmDev<T> d, const int4* __restrict__ tiles, const int* __restrict__ cells,
+                               const int64_t* __restrict__ level_off, const int* __restrict__ csr,
+                               const C<T>* __restrict__ buf, int accumulate) {
+  const int4 tile = tiles[blockIdx.x];
+  const int P = d.P;
+  const int64_t off = level_off[tile.x];
+  for (int e = threadIdx.x; e < tile.w * P; e += blockDim.x) {
+    int c = e / P, a = e - c * P;
+    int lo = csr[tile.z + c], hi = csr[tile.z + c + 1];
+    C<T> v = mkc<T>(0, 0);
+    for (int q = lo; q < hi; ++q) v = cadd<T>(v, buf[(int64_t)q * P + a]);
+    C<T>* dst = d.Lc + (off + cells[tile.z + c]) * P + a;
+    *dst = accumulate ? cadd<T>(*dst, v) : v;
+  }
+}
+
+// builds the pair lists of (target mask tm, source mask sm) on first use
+int m2l_pair_lists(fmm_tree* t, int sm, int tm, size_t csz, cudaStream_t s) {
+  const int ci = (tm - 1) * 3 + (sm - 1);
+  if (t->pr_csr[ci]) return HFMM_OK;
+  const int mi = tm - 1;
+  const int nt = t->m2l_ntiles[mi];
+  const int64_t ncell = t->total_cells;  // tile cells index the cells array of the mask
+  int* cnt = nullptr;
+  HFMM_TRY(tree_alloc_t(t, &t->pr_csr[ci], ncell + 1));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&cnt, sizeof(int) * (ncell + 1), s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * (ncell + 1), s));
+  if (nt) k_pairs_list<<<nt, 32, 0, s>>>(t->m2l_tiles[mi], t->m2l_cells[mi], t->flags, t->level_off_dev, t->m2l_off,
+                                         t->m2l_box_index, t->m2l_count, sm, cnt, nullptr, nullptr, nullptr,
+                                         nullptr, (int)t->box_cells);
+  k_scan_counts<<<1, 1024, 0, s>>>(cnt, (int)ncell, t->pr_csr[ci]);
+  HFMM_TRY(hfmm_last_launch());
+  int np = 0;
+  HFMM_CUDA_TRY(cudaMemcpyAsync(&np, t->pr_csr[ci] + ncell, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  t->pr_npairs[ci] = np;
+  const int nkeys = (t->L + 1) * (int)t->box_cells;
+  int *pkey = nullptr, *kcnt = nullptr, *kstart = nullptr;
+  HFMM_TRY(tree_alloc_t(t, &t->pr_tgt[ci], (size_t)np + 1));
+  HFMM_TRY(tree_alloc_t(t, &t->pr_src[ci], (size_t)np + 1));
+  HFMM_TRY(tree_alloc_t(t, &t->pr_grouped[ci], (size_t)np + 1));
+  HFMM_TRY(tree_alloc_t(t, &t->pr_chunks[ci], (size_t)np / 32 + nkeys + 1));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&pkey, sizeof(int) * ((size_t)np + 1), s));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&kcnt, sizeof(int) * (nkeys + 1), s));
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&kstart, sizeof(int) * (nkeys + 2), s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(kcnt, 0, sizeof(int) * (nkeys + 1), s));
+  if (nt)
+    k_pairs_list<<<nt, 32, 0, s>>>(t->m2l_tiles[mi], t->m2l_cells[mi], t->flags, t->level_off_dev, t->m2l_off,
+                                   t->m2l_box_index, t->m2l_count, sm, nullptr, t->pr_csr[ci], t->pr_tgt[ci],
+                                   t->pr_src[ci], pkey, (int)t->box_cells);
+  if (np) k_count_keys<<<ceil_div(np, 256), 256, 0, s>>>(np, pkey, kcnt);
+  k_scan_counts<<<1, 1024, 0, s>>>(kcnt, nkeys, kstart);
+  HFMM_CUDA_TRY(cudaMemcpyAsync(kcnt, kstart, sizeof(int) * nkeys, cudaMemcpyDeviceToDevice, s));
+  if (np) k_pairs_group<<<ceil_div(np, 256), 256, 0, s>>>(np, pkey, kcnt, t->pr_grouped[ci]);
+  int* d_n = kcnt + nkeys;
+  k_pairs_chunks<<<1, 1, 0, s>>>(nkeys, (int)t->box_cells, kstart, t->pr_chunks[ci], d_n);
+  HFMM_TRY(hfmm_last_launch());
+  int nchunks = 0;
+  HFMM_CUDA_TRY(cudaMemcpyAsync(&nchunks, d_n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  t->pr_nchunks[ci] = nchunks;
+  cudaFreeAsync(cnt, s);
+  cudaFreeAsync(pkey, s);
+  cudaFreeAsync(kcnt, s);
+  cudaFreeAsync(kstart, s);
+  if (np > t->pr_buf_pairs) {  // product buffer sized for the largest list
+    HFMM_TRY(tree_alloc(t, &t->pr_buf, csz * (size_t)np * t->P));
+    t->pr_buf_pairs = np;
+  }
+  count_launches(6);
+  return HFMM_OK;
+}
+
+template <typename T, int R, int CM, int RT>
+int launch_m2l_pairs_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
+                        int accumulate, cudaStream_t s) {
+  const int P = t->P, mi = tgt_set - 1, ci = mi * 3 + (src_set - 1);
+  HFMM_TRY(m2l_pair_lists(t, src_set, tgt_set, sizeof(C<T>), s));
+  const int TC = 8 * CM;
+  const size_t sm = 256 + ((size_t)P * P + (size_t)TC * (P + 2)) * sizeof(C<T>);
+  C<T>* buf = reinterpret_cast<C<T>*>(t->pr_buf);
+  if (t->pr_nchunks[ci] > 0) {
+    HFMM_TRY(set_smem<T>((const void*)k_m2l_pairs<T, R, CM, RT>, sm));
+    k_m2l_pairs<T, R, CM, RT><<<t->pr_nchunks[ci], RT * 8, sm, s>>>(
+        d, t->pr_chunks[ci], t->pr_grouped[ci], t->pr_src[ci], t->level_off_dev, ops, t->box_cells, buf);
+  }
+  if (t->m2l_ntiles[mi] > 0)
+    k_pairs_reduce<T><<<t->m2l_ntiles[mi], 128, 0, s>>>(d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev,
+                                                        t->pr_csr[ci], buf, accumulate);
+  count_launches(2);
+  return hfmm_last_launch();
+}
+
+template <typename T>
+int launch_m2l_pairs(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set, int accumulate,
+                     cudaStream_t s) {
+  const int P = t->P;
+  if (P <= 16) return launch_m2l_pairs_rt<T, 1, 4, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 32) return launch_m2l_pairs_rt<T, 2, 4, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 36) return launch_m2l_pairs_rt<T, 3, 4, 12>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 48) return launch_m2l_pairs_rt<T, 3, 4, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 64) return launch_m2l_pairs_rt<T, 4, 4, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 96) return launch_m2l_pairs_rt<T, 6, 4, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  return HFMM_ERR_UNSUPPORTED;
+}
+
 template <typename T, int CM, int R, int RT>
 int launch_m2l_tma_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
                       int accumulate, cudaStream_t s) {
@@ -1409,6 +1676,11 @@ int m2l_stage(fmm_tree* t, const FmmDev<T>& d, const C<T>* m2l, int src_set, int
   const bool tma = tiled && (P % 2 == 0);  // rows are 16-byte multiples; pairs of columns per load
   if (tma) {
     *nlaunch = 0;  // counted by the launcher
+    const int ci = (tgt_set - 1) * 3 + (src_set - 1);
+    const bool pairs = t->tuned_variant[ci] >= 0 ? t->tuned_variant[ci] == 2
+                                                 : (t->m2l_pairs_enabled && tgt_set == HFMM_SET_BND &&
+                                                    src_set == HFMM_SET_BND);
+    if (pairs) return launch_m2l_pairs<T>(t, d, m2l, src_set, tgt_set, accumulate, s);
     if (t->m2l_tc == 32) return launch_m2l_tma<T, 4>(t, d, m2l, src_set, tgt_set, accumulate, s);
     return launch_m2l_tma<T, 2>(t, d, m2l, src_set, tgt_set, accumulate, s);
   }

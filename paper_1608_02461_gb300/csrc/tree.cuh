@@ -123,6 +123,20 @@ struct fmm_tree {
   unsigned* m2l_vmask[9] = {};
   int* m2l_nval[9] = {};
   void* zero_row = nullptr;     // P complex zeros (bulk-copy source for empty columns)
+  // pair-list M2L for sparse passes, per (target mask, source mask) pair:
+  // the valid (target, source) cell pairs in target-major order (CSR over the
+  // tile cells), the same pairs grouped by (level, operator slot) in chunks
+  // of at most 32, and a product buffer with one row per pair
+  int* pr_tgt[9] = {};          // [npairs] level-local target cell (CSR order)
+  int* pr_src[9] = {};          // [npairs] level-local source cell
+  int* pr_csr[9] = {};          // [ncells + 1] pair range of each tile cell (cells in tile order)
+  int* pr_grouped[9] = {};      // [npairs] pair indices grouped by (level, slot)
+  int4* pr_chunks[9] = {};      // {level, slot, first (grouped), count}
+  int pr_nchunks[9] = {};
+  int64_t pr_npairs[9] = {};
+  void* pr_buf = nullptr;       // [max npairs][P] products (precision T)
+  int64_t pr_buf_pairs = 0;
+  int m2l_pairs_enabled = 1;    // allow the pair-list form for boundary-target passes
   void* m2l_part = nullptr;     // [m2l_part_max][total_cells][P] split-offset partial sums
   int m2l_part_max = 1;
   int m2l_variant = 1;          // 1: warp-specialised pipeline, 0: two-stage block pipeline

