@@ -124,6 +124,7 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   HFMM_TRY(build_operators(t, s));
   HFMM_TRY(build_pair_counts(t, s));
   HFMM_TRY(build_m2l_tiles(t, s));
+  HFMM_TRY(build_active_lists(t, s));
   HFMM_CUDA_TRY(cudaEventCreate(&t->ev0));
   HFMM_CUDA_TRY(cudaEventCreate(&t->ev1));
   HFMM_CUDA_TRY(cudaStreamSynchronize(s));

@@ -18,6 +18,12 @@ namespace {
 template <typename T>
 int set_smem(const void* fn, size_t bytes);
 
+// cells of level l holding points of a set mask (count, device list)
+inline int act_n(const fmm_tree* t, int mask, int l) { return t->act_count[mask - 1][l]; }
+inline const int* act_list(const fmm_tree* t, int mask, int l) {
+  return t->act_cells[mask - 1] + t->level_off[l];
+}
+
 template <typename T>
 struct FmmDev {
   const double* xyz;     // sorted coordinates, FP64
@@ -129,10 +135,11 @@ __device__ void regular_basis_dk_conj(int p, T k, T dx, T dy, T dz, C<T> q, C<T>
 // summed per coefficient.  Output Mout (leaf level), weights times `fac`;
 // DK: derivative of the basis with respect to k.
 template <typename T, bool DK>
-__global__ void k_p2m(FmmDev<T> d, C<T>* Mout, int64_t leaf_off, int src_set, int chunk, C<T> fac) {
+__global__ void k_p2m(FmmDev<T> d, C<T>* Mout, int64_t leaf_off, int src_set, int chunk, C<T> fac,
+                      const int* __restrict__ list) {
   extern __shared__ unsigned char smem_raw[];
   C<T>* basis = reinterpret_cast<C<T>*>(smem_raw);
-  const int leaf = blockIdx.x;
+  const int leaf = list ? list[blockIdx.x] : blockIdx.x;
   const int P = d.P;
   C<T>* M = Mout + (leaf_off + leaf) * P;
   int lo, hi;
@@ -183,12 +190,18 @@ __device__ __forceinline__ C<T> matvec_row(const C<T>* Tcol, int ap, const C<T>*
   return acc;
 }
 
+// Mout(parent) (+)= sum over children holding sources of T_o Min(child).
+// With a list, only the listed parents (those holding sources) are visited;
+// expansions of cells without sources are never read (they may be stale).
+// Four threads per output row (thread `sub` takes octants sub and sub + 4),
+// combined with warp shuffles; block = 4 P threads rounded up to a warp.
 template <typename T>
 __global__ void k_m2m(FmmDev<T> d, int level, int64_t off_par, int64_t off_child, const C<T>* Min, C<T>* Mout,
-                      const C<T>* ops, int src_set, int accumulate) {
+                      const C<T>* __restrict__ ops, int src_set, int accumulate, const int* __restrict__ list) {
   extern __shared__ unsigned char smem_raw[];
-  C<T>* xs = reinterpret_cast<C<T>*>(smem_raw);
-  const int cell = blockIdx.x;
+  C<T>* xs = reinterpret_cast<C<T>*>(smem_raw);  // [8][P]
+  __shared__ int has[8];
+  const int cell = list ? list[blockIdx.x] : blockIdx.x;
   const int P = d.P;
   C<T>* Mp = Mout + (off_par + cell) * P;
   if (!(d.flags[off_par + cell] & src_set)) {
@@ -196,35 +209,58 @@ __global__ void k_m2m(FmmDev<T> d, int level, int64_t off_par, int64_t off_child
       for (int a = threadIdx.x; a < P; a += blockDim.x) Mp[a] = mkc<T>(0, 0);
     return;
   }
-  for (int e = threadIdx.x; e < 8 * P; e += blockDim.x) xs[e] = Min[(off_child + 8 * (int64_t)cell) * P + e];
+  if (threadIdx.x < 8) has[threadIdx.x] = (d.flags[off_child + 8 * (int64_t)cell + threadIdx.x] & src_set) != 0;
   __syncthreads();
-  for (int ap = threadIdx.x; ap < P; ap += blockDim.x) {
-    C<T> acc = accumulate ? Mp[ap] : mkc<T>(0, 0);
-    for (int o = 0; o < 8; ++o) {
-      C<T> v = matvec_row<T>(ops + (int64_t)o * P * P, ap, xs + o * P, P);
-      acc = cadd<T>(acc, v);
-    }
-    Mp[ap] = acc;
+  const C<T>* ch = Min + (off_child + 8 * (int64_t)cell) * P;
+  for (int o = 0; o < 8; ++o) {
+    const bool h = has[o];
+    for (int a = threadIdx.x; a < P; a += blockDim.x) xs[o * P + a] = h ? ch[o * P + a] : mkc<T>(0, 0);
   }
+  __syncthreads();
+  const int ap = threadIdx.x >> 2, sub = threadIdx.x & 3;
+  C<T> acc = mkc<T>(0, 0);
+  if (ap < P) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int o = sub + 4 * q;
+      if (!has[o]) continue;
+      const C<T>* Tc = ops + (int64_t)o * P * P + ap;
+      const C<T>* x = xs + o * P;
+      for (int a = 0; a < P; ++a) cfma<T>(acc, Tc[(int64_t)a * P], x[a]);
+    }
+  }
+  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+  if (ap < P && sub == 0) Mp[ap] = accumulate ? cadd<T>(Mp[ap], acc) : acc;
 }
 
-// Lout(child) += T_octant Lin(parent)
+// Lout(child) += T_octant Lin(parent); four threads per output row, each a
+// quarter of the columns, combined with warp shuffles
 template <typename T>
 __global__ void k_l2l(FmmDev<T> d, int64_t off_par, int64_t off_child, const C<T>* Lin, C<T>* Lout,
-                      const C<T>* ops, int tgt_set) {
+                      const C<T>* __restrict__ ops, int tgt_set, const int* __restrict__ list) {
   extern __shared__ unsigned char smem_raw[];
   C<T>* xs = reinterpret_cast<C<T>*>(smem_raw);
-  const int cell = blockIdx.x;  // child
+  const int cell = list ? list[blockIdx.x] : blockIdx.x;  // child
   const int P = d.P;
   if (!(d.flags[off_child + cell] & tgt_set)) return;
   const int parent = cell >> 3, o = cell & 7;
   for (int e = threadIdx.x; e < P; e += blockDim.x) xs[e] = Lin[(off_par + parent) * P + e];
   __syncthreads();
   C<T>* Lch = Lout + (off_child + cell) * P;
-  for (int ap = threadIdx.x; ap < P; ap += blockDim.x) {
-    C<T> v = matvec_row<T>(ops + (int64_t)o * P * P, ap, xs, P);
-    Lch[ap] = cadd<T>(Lch[ap], v);
+  const int ap = threadIdx.x >> 2, sub = threadIdx.x & 3;
+  C<T> acc = mkc<T>(0, 0);
+  if (ap < P) {
+    const C<T>* Tc = ops + (int64_t)o * P * P + ap;
+    for (int a = sub; a < P; a += 4) cfma<T>(acc, Tc[(int64_t)a * P], xs[a]);
   }
+  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+  if (ap < P && sub == 0) Lch[ap] = cadd<T>(Lch[ap], acc);
 }
 
 // ---------------------------------------------------------------- M2L
@@ -1199,10 +1235,10 @@ int launch_m2l_tiled(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, const int
 // ---------------------------------------------------------------- L2P
 // phi_i = fac * sum_a L_a R_a(x_i - c)   (forward fac = i k; adjoint fac = 1)
 template <typename T>
-__global__ void k_l2p(FmmDev<T> d, int64_t leaf_off, int tgt_set, C<T> fac) {
+__global__ void k_l2p(FmmDev<T> d, int64_t leaf_off, int tgt_set, C<T> fac, const int* __restrict__ list) {
   extern __shared__ unsigned char smem_raw[];
   C<T>* Ls = reinterpret_cast<C<T>*>(smem_raw);
-  const int leaf = blockIdx.x;
+  const int leaf = list ? list[blockIdx.x] : blockIdx.x;
   const int P = d.P;
   int lo, hi;
   leaf_range(d.leaf_start, d.leaf_mid, leaf, tgt_set, lo, hi);
@@ -1243,10 +1279,10 @@ __global__ void k_l2p(FmmDev<T> d, int64_t leaf_off, int tgt_set, C<T> fac) {
 // dR_a/dk = |v| j_n'(k|v|) Y_a (tangent of L2P, written to `out`)
 template <typename T>
 __global__ void k_l2p_dk(FmmDev<T> d, const C<T>* __restrict__ Lv, const C<T>* __restrict__ Ldv,
-                         C<T>* __restrict__ out, int64_t leaf_off, int tgt_set) {
+                         C<T>* __restrict__ out, int64_t leaf_off, int tgt_set, const int* __restrict__ list) {
   extern __shared__ unsigned char smem_raw[];
   C<T>* Ls = reinterpret_cast<C<T>*>(smem_raw);
-  const int leaf = blockIdx.x;
+  const int leaf = list ? list[blockIdx.x] : blockIdx.x;
   const int P = d.P;
   int lo, hi;
   leaf_range(d.leaf_start, d.leaf_mid, leaf, tgt_set, lo, hi);
@@ -1438,13 +1474,14 @@ __device__ __forceinline__ T rsqrt_t(T x) {
 template <typename T, int W, int KMODE>
 __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restrict__ near_off,
                                                 int near_count, int src_set, int tgt_set,
-                                                double2 sig_vol, double2 sig_bnd) {
+                                                double2 sig_vol, double2 sig_bnd,
+                                                const int* __restrict__ list) {
   __shared__ StagedSrc<T> spos[W];
   __shared__ C<T> sq[W];
   __shared__ int nb_leaf[128], nb_lo[128], nb_cnt[128], nb_pre[129];
   __shared__ T nb_sh[128][3];
   __shared__ int n_nb;
-  const int leaf = blockIdx.x;
+  const int leaf = list ? list[blockIdx.x] : blockIdx.x;
   int tlo, thi;
   leaf_range(d.leaf_start, d.leaf_mid, leaf, tgt_set, tlo, thi);
   const int ntgt = thi - tlo;
@@ -1651,10 +1688,9 @@ FmmDev<T> make_dev(fmm_tree* t) {
   return d;
 }
 
-int threads_for(int P) {
-  int th = ((P + 31) / 32) * 32;
-  if (th > 256) th = 256;
-  if (th < 32) th = 32;
+int threads_for(int P) {  // four threads per expansion coefficient (M2M / L2L)
+  int th = ((4 * P + 31) / 32) * 32;
+  if (th > 1024) th = 1024;
   return th;
 }
 
@@ -1705,8 +1741,10 @@ int p2p_stage(fmm_tree* t, const FmmDev<T>& d, int src_set, int tgt_set, double2
               cudaStream_t s) {
   const int nleaf = 1 << (3 * t->L);
   if (t->near_count <= 128) {
-    k_p2p_v2<T, (sizeof(T) == 4 ? 1536 : 768), KMODE><<<nleaf, 256, 0, s>>>(d, t->near_off, t->near_count,
-                                                                            src_set, tgt_set, sv, sb);
+    const int na = act_n(t, tgt_set, t->L);
+    if (na)
+      k_p2p_v2<T, (sizeof(T) == 4 ? 1536 : 768), KMODE><<<na, 256, 0, s>>>(
+          d, t->near_off, t->near_count, src_set, tgt_set, sv, sb, act_list(t, tgt_set, t->L));
     return hfmm_last_launch();
   }
   if (KMODE != 0) return HFMM_ERR_UNSUPPORTED;
@@ -1733,7 +1771,6 @@ int core_adjoint_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   HFMM_TRY(build_operators_adjoint(t, s));
   FmmDev<T> d = make_dev<T>(t);
   const int P = t->P, L = t->L;
-  const int nleaf = 1 << (3 * L);
   const int64_t PP = (int64_t)P * P;
   const int th = threads_for(P);
   const C<T>* m2m_h = ops_of<T>(t, t->op_m2m_h, t->op_m2m_h32);
@@ -1745,12 +1782,14 @@ int core_adjoint_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   const int chunk = 32;
   size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
   HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
-  k_p2m<T, false><<<nleaf, 64, sm_p2m, s>>>(d, Lh, t->level_off[L], Sp, chunk, mkc<T>(0, -d.k));
+  if (act_n(t, Sp, L))
+    k_p2m<T, false><<<act_n(t, Sp, L), 64, sm_p2m, s>>>(d, Lh, t->level_off[L], Sp, chunk, mkc<T>(0, -d.k), act_list(t, Sp, L));
   size_t sm8 = 8 * (size_t)P * sizeof(C<T>);
   HFMM_TRY(set_smem<T>((const void*)k_m2m<T>, sm8));
   for (int l = L - 1; l >= 2; --l)
-    k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], Lh, Lh,
-                                            l2l_h + (int64_t)l * 8 * PP, Sp, 0);
+    if (act_n(t, Sp, l))
+      k_m2m<T><<<act_n(t, Sp, l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], Lh, Lh,
+                                            l2l_h + (int64_t)l * 8 * PP, Sp, 0, act_list(t, Sp, l));
   FmmDev<T> dm = d;
   dm.M = Lh;
   dm.Lc = Mh;
@@ -1758,11 +1797,13 @@ int core_adjoint_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   HFMM_TRY(m2l_stage<T>(t, dm, m2l_h, Sp, Tp, 0, s, &nm));
   size_t sm1 = (size_t)P * sizeof(C<T>);
   for (int l = 2; l < L; ++l)
-    k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], Mh, Mh,
-                                                  m2m_h + (int64_t)l * 8 * PP, Tp);
+    if (act_n(t, Tp, l + 1))
+      k_l2l<T><<<act_n(t, Tp, l + 1), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], Mh, Mh,
+                                                  m2m_h + (int64_t)l * 8 * PP, Tp, act_list(t, Tp, l + 1));
   FmmDev<T> dl = d;
   dl.Lc = Mh;
-  k_l2p<T><<<nleaf, 64, sm1, s>>>(dl, t->level_off[L], Tp, mkc<T>(1, 0));
+  if (act_n(t, Tp, L))
+    k_l2p<T><<<act_n(t, Tp, L), 64, sm1, s>>>(dl, t->level_off[L], Tp, mkc<T>(1, 0), act_list(t, Tp, L));
   const double2 cv = make_double2(t->sigma_vol.x, -t->sigma_vol.y);
   const double2 cb = make_double2(t->sigma_bnd.x, -t->sigma_bnd.y);
   HFMM_TRY(p2p_stage<T, 1>(t, d, Sp, Tp, cv, cb, s));
@@ -1790,7 +1831,6 @@ int core_dk_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
     HFMM_CUDA_TRY(cudaMemsetAsync(t->Ld, 0, csz * t->total_cells * P, s));
   }
   FmmDev<T> d = make_dev<T>(t);
-  const int nleaf = 1 << (3 * L);
   const int64_t PP = (int64_t)P * P;
   const int th = threads_for(P);
   const C<T>* m2m = ops_of<T>(t, t->op_m2m, t->op_m2m32);
@@ -1806,18 +1846,23 @@ int core_dk_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   size_t sm_p2m = (size_t)chunk * P * csz;
   HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
   HFMM_TRY(set_smem<T>((const void*)k_p2m<T, true>, sm_p2m));
-  k_p2m<T, false><<<nleaf, 64, sm_p2m, s>>>(d, d.M, t->level_off[L], src_set, chunk, mkc<T>(1, 0));
-  k_p2m<T, true><<<nleaf, 64, sm_p2m, s>>>(d, Md, t->level_off[L], src_set, chunk, mkc<T>(1, 0));
+  if (act_n(t, src_set, L))
+    k_p2m<T, false><<<act_n(t, src_set, L), 64, sm_p2m, s>>>(d, d.M, t->level_off[L], src_set, chunk, mkc<T>(1, 0), act_list(t, src_set, L));
+  if (act_n(t, src_set, L))
+    k_p2m<T, true><<<act_n(t, src_set, L), 64, sm_p2m, s>>>(d, Md, t->level_off[L], src_set, chunk, mkc<T>(1, 0), act_list(t, src_set, L));
   size_t sm8 = 8 * (size_t)P * csz;
   HFMM_TRY(set_smem<T>((const void*)k_m2m<T>, sm8));
   for (int l = L - 1; l >= 2; --l) {
     const int64_t o = (int64_t)l * 8 * PP;
-    k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], d.M, d.M, m2m + o,
-                                            src_set, 0);
-    k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], Md, Md, m2m + o,
-                                            src_set, 0);
-    k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], d.M, Md, m2m_d + o,
-                                            src_set, 1);
+    if (act_n(t, src_set, l))
+      k_m2m<T><<<act_n(t, src_set, l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], d.M, d.M, m2m + o,
+                                            src_set, 0, act_list(t, src_set, l));
+    if (act_n(t, src_set, l))
+      k_m2m<T><<<act_n(t, src_set, l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], Md, Md, m2m + o,
+                                            src_set, 0, act_list(t, src_set, l));
+    if (act_n(t, src_set, l))
+      k_m2m<T><<<act_n(t, src_set, l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], d.M, Md, m2m_d + o,
+                                            src_set, 1, act_list(t, src_set, l));
   }
   int n1 = 0, n2 = 0, n3 = 0;
   HFMM_TRY(m2l_stage<T>(t, d, m2l, src_set, tgt_set, 0, s, &n1));  // L
@@ -1831,14 +1876,19 @@ int core_dk_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   size_t sm1 = (size_t)P * csz;
   for (int l = 2; l < L; ++l) {
     const int64_t o = (int64_t)l * 8 * PP;
-    k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], d.Lc, d.Lc, l2l + o,
-                                                  tgt_set);
-    k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], Ld, Ld, l2l + o,
-                                                  tgt_set);
-    k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], d.Lc, Ld,
-                                                  l2l_d + o, tgt_set);
+    if (act_n(t, tgt_set, l + 1))
+      k_l2l<T><<<act_n(t, tgt_set, l + 1), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], d.Lc, d.Lc, l2l + o,
+                                                  tgt_set, act_list(t, tgt_set, l + 1));
+    if (act_n(t, tgt_set, l + 1))
+      k_l2l<T><<<act_n(t, tgt_set, l + 1), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], Ld, Ld, l2l + o,
+                                                  tgt_set, act_list(t, tgt_set, l + 1));
+    if (act_n(t, tgt_set, l + 1))
+      k_l2l<T><<<act_n(t, tgt_set, l + 1), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], d.Lc, Ld,
+                                                  l2l_d + o, tgt_set, act_list(t, tgt_set, l + 1));
   }
-  k_l2p_dk<T><<<nleaf, 64, 2 * sm1, s>>>(d, d.Lc, Ld, phd, t->level_off[L], tgt_set);
+  if (act_n(t, tgt_set, L))
+    k_l2p_dk<T><<<act_n(t, tgt_set, L), 64, 2 * sm1, s>>>(d, d.Lc, Ld, phd, t->level_off[L], tgt_set,
+                                                          act_list(t, tgt_set, L));
   FmmDev<T> dp = d;
   dp.phis = phd;
   HFMM_TRY(p2p_stage<T, 2>(t, dp, src_set, tgt_set, t->dsigma_vol, t->dsigma_bnd, s));
@@ -1864,7 +1914,8 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
   HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
   tm.begin(HFMM_STAGE_P2M, s);
-  k_p2m<T, false><<<nleaf, 64, sm_p2m, s>>>(d, d.M, t->level_off[L], src_set, chunk, mkc<T>(1, 0));
+  if (act_n(t, src_set, L))
+    k_p2m<T, false><<<act_n(t, src_set, L), 64, sm_p2m, s>>>(d, d.M, t->level_off[L], src_set, chunk, mkc<T>(1, 0), act_list(t, src_set, L));
   tm.end(1, s);
   count_launches(1);
   // M2M, levels L-1 .. 2
@@ -1873,8 +1924,9 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   if (L > 2) {
     tm.begin(HFMM_STAGE_M2M, s);
     for (int l = L - 1; l >= 2; --l)
-      k_m2m<T><<<1 << (3 * l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], d.M, d.M,
-                                              m2m + (int64_t)l * 8 * PP, src_set, 0);
+      if (act_n(t, src_set, l))
+      k_m2m<T><<<act_n(t, src_set, l), th, sm8, s>>>(d, l, t->level_off[l], t->level_off[l + 1], d.M, d.M,
+                                              m2m + (int64_t)l * 8 * PP, src_set, 0, act_list(t, src_set, l));
     tm.end(L - 2, s);
     count_launches(L - 2);
   }
@@ -1889,14 +1941,17 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   if (L > 2) {
     tm.begin(HFMM_STAGE_L2L, s);
     for (int l = 2; l < L; ++l)
-      k_l2l<T><<<1 << (3 * (l + 1)), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], d.Lc, d.Lc,
-                                                    l2l + (int64_t)l * 8 * PP, tgt_set);
+      if (act_n(t, tgt_set, l + 1))
+      k_l2l<T><<<act_n(t, tgt_set, l + 1), th, sm1, s>>>(d, t->level_off[l], t->level_off[l + 1], d.Lc, d.Lc,
+                                                    l2l + (int64_t)l * 8 * PP, tgt_set, act_list(t, tgt_set, l + 1));
     tm.end(L - 2, s);
     count_launches(L - 2);
   }
   // L2P then P2P (adds)
   tm.begin(HFMM_STAGE_L2P, s);
-  k_l2p<T><<<nleaf, 64, sm1, s>>>(d, t->level_off[L], tgt_set, mkc<T>(0, d.k));
+  if (act_n(t, tgt_set, L))
+    k_l2p<T><<<act_n(t, tgt_set, L), 64, sm1, s>>>(d, t->level_off[L], tgt_set, mkc<T>(0, d.k),
+                                                    act_list(t, tgt_set, L));
   tm.end(1, s);
   tm.begin(HFMM_STAGE_P2P, s);
   HFMM_TRY(p2p_stage<T, 0>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));

@@ -222,6 +222,22 @@ __global__ void k_m2l_slots(int box, const int* count, int* off, int* box_index,
   *nslots = ns;
 }
 
+// ---- active cells: one thread per (level, mask), Morton order
+
+__global__ void k_active_cells(int L, const int* flags, const int64_t* level_off, int64_t stride, int* cells,
+                               int* counts) {
+  const int l = blockIdx.x, mi = threadIdx.x;
+  if (mi >= 3 || l > L) return;
+  const int mask = mi + 1;
+  const int64_t off = level_off[l];
+  const int nc = 1 << (3 * l);
+  int* out = cells + mi * stride + off;
+  int c = 0;
+  for (int i = 0; i < nc; ++i)
+    if (flags[off + i] & mask) out[c++] = i;
+  counts[mi * (HFMM_MAX_LEVEL + 1) + l] = c;
+}
+
 // ---- M2L target tiles
 
 // cells of level 2 + blockIdx.x whose flags meet mask blockIdx.y + 1, one
@@ -680,6 +696,26 @@ int build_m2l_tiles(fmm_tree* t, cudaStream_t s) {
     t->m2l_cells[i] = cells + i * cstride;
     t->m2l_tiles[i] = tiles + i * tstride;
     t->m2l_ntiles[i] = nt[i];
+  }
+  return HFMM_OK;
+}
+
+int build_active_lists(fmm_tree* t, cudaStream_t s) {
+  int* cells = nullptr;
+  HFMM_TRY(tree_alloc_t(t, &cells, 3 * t->total_cells));
+  int* d_cnt = nullptr;
+  const int nc = 3 * (HFMM_MAX_LEVEL + 1);
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&d_cnt, sizeof(int) * nc, s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, sizeof(int) * nc, s));
+  k_active_cells<<<t->L + 1, 32, 0, s>>>(t->L, t->flags, t->level_off_dev, t->total_cells, cells, d_cnt);
+  HFMM_TRY(hfmm_last_launch());
+  int h[3 * (HFMM_MAX_LEVEL + 1)];
+  HFMM_CUDA_TRY(cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFreeAsync(d_cnt, s);
+  for (int m = 0; m < 3; ++m) {
+    t->act_cells[m] = cells + m * t->total_cells;
+    for (int l = 0; l <= HFMM_MAX_LEVEL; ++l) t->act_count[m][l] = h[m * (HFMM_MAX_LEVEL + 1) + l];
   }
   return HFMM_OK;
 }

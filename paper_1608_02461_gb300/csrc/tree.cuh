@@ -103,6 +103,11 @@ struct fmm_tree {
   int64_t* level_off_dev = nullptr;             // device copy
   int64_t total_cells = 0;
 
+  // cells of each level holding points of a set mask (index mask - 1), in
+  // Morton order at level_off[l]; counts on the host for grid sizes
+  int* act_cells[3] = {nullptr, nullptr, nullptr};
+  int act_count[3][HFMM_MAX_LEVEL + 1] = {};
+
   // ---- interaction lists (offsets in cell units)
   int near_count = 0;
   int* near_off = nullptr;      // [near_count] packed offsets (dx,dy,dz) each in 8 bits + 128
@@ -211,6 +216,7 @@ int build_lists(fmm_tree* t, cudaStream_t s);
 int build_self_terms(fmm_tree* t, cudaStream_t s);
 int build_pair_counts(fmm_tree* t, cudaStream_t s);
 int build_m2l_tiles(fmm_tree* t, cudaStream_t s);
+int build_active_lists(fmm_tree* t, cudaStream_t s);
 double p2p_work(const fmm_tree* t, int src_set, int tgt_set);
 double m2l_work(const fmm_tree* t, int src_set, int tgt_set);
 
