@@ -256,17 +256,30 @@ int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_x, int coun
  */
 int fmm_autotune(fmm_tree* tree, void* stream);
 
+/*
+ * fmm_use_graphs -- enable (1, default) or disable (0) the CUDA-graph form of
+ * the preconditioner inside gmres_solve: Pass A, one inner GMRES cycle of
+ * inner_maxit steps driven on the device (steps after convergence return at
+ * once through a device flag) and Pass C are captured once per (inner_rtol,
+ * inner_maxit) and replayed with one launch per application, with no host
+ * synchronisation inside.  Used when inner_m >= inner_maxit; results are
+ * identical to the host-driven form.
+ */
+int fmm_use_graphs(fmm_tree* tree, int enable);
+
 /* Sizes and counters of a built tree.  Waits for the handle's pending
  * timing events (host blocks until they complete). */
 int fmm_get_stats(const fmm_tree* tree, hfmm_stats* stats);
 
 /*
- * fmm_set_timing -- switch per-stage CUDA-event timing on (1) or off (0) for
- * the handle and reset the stage accumulators.  While on, every stage launch
- * is bracketed by events on the launching stream; fmm_get_stats resolves
- * them.  Costs two event records per stage and no synchronisation.
+ * fmm_set_timing -- per-stage CUDA-event timing.  `stage_mask` has bit i set
+ * for every stage HFMM_STAGE_i to time (0 switches timing off; (1 << 8) - 1
+ * times all stages); the stage accumulators are reset.  While on, each timed
+ * stage's launches are bracketed by events on the launching stream;
+ * fmm_get_stats resolves them.  Costs two event records per timed stage and
+ * no synchronisation.
  */
-int fmm_set_timing(fmm_tree* tree, int enable);
+int fmm_set_timing(fmm_tree* tree, int stage_mask);
 
 /*
  * hfmm_direct_sum_noalloc -- allocation-free direct Helmholtz sum.

@@ -10,10 +10,42 @@
 #include "krylov.cuh"
 #include "tree.cuh"
 
+// The preconditioner as one CUDA graph: Pass A, one device-driven inner
+// GMRES cycle (its late steps skipped after convergence through a device
+// flag), Pass C; on fixed input/output buffers.  Captured on a private
+// stream, replayed on the caller's.
+struct PrecGraph {
+  cudaGraphExec_t exec = nullptr;
+  double rtol = -1.0;
+  int maxit = -1;
+  int timer_mask = -1;
+  int eager_its = 0;            // inner steps of the eager apply that preceded a capture
+  double2* r_in = nullptr;
+  double2* z_out = nullptr;
+  int* flags = nullptr;         // [0] done, [1] steps of the last cycle, [2] steps summed over replays
+  int64_t kernels = 0;          // kernel nodes per replay
+  std::vector<TimerSlot> slots; // timed stages inside the graph
+  bool pending = false;         // slots of the last replay not yet resolved
+  cudaStream_t cap = nullptr;
+};
+
 struct fmm_tree_ext {
   GmresWork inner;   // boundary solve V q = -g
+  GmresWork inner_g; // the same in the graph form
   GmresWork outer;   // A x = b
+  PrecGraph pg;
 };
+
+static void prec_graph_drop(PrecGraph& G) {
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G.exec = nullptr;
+  for (auto& sl : G.slots) {
+    cudaEventDestroy(sl.a);
+    cudaEventDestroy(sl.b);
+  }
+  G.slots.clear();
+  G.pending = false;
+}
 
 namespace {
 
@@ -112,6 +144,7 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   // M2L pipeline: the warp-specialised form wins once the operator is large
   // (p >= 8), the block-synchronous two-stage form below that (measured)
   t->m2l_variant = P >= 64 ? 1 : 0;
+  if (const char* g = getenv("HFMM_GRAPHS")) t->use_graphs = atoi(g) != 0;
   if (const char* v = getenv("HFMM_M2L_VARIANT")) t->m2l_variant = atoi(v);
   HFMM_TRY(tree_alloc(t, &t->m2l_part, csz * t->total_cells * P * t->m2l_part_max));
   HFMM_TRY(tree_alloc_t(t, &t->g_bnd, t->n_bnd + 1));
@@ -201,7 +234,10 @@ extern "C" void fmm_destroy_tree(fmm_tree* tree) {
   cudaDeviceSynchronize();
   fmm_tree_ext* e = ext_of(tree);
   gmres_work_free(e->inner);
+  gmres_work_free(e->inner_g);
   gmres_work_free(e->outer);
+  prec_graph_drop(e->pg);
+  if (e->pg.cap) cudaStreamDestroy(e->pg.cap);
   release(tree);
   delete e;
   delete tree;
@@ -267,6 +303,91 @@ static int precond_impl(fmm_tree* t, const double2* r, double2* z, double inner_
   return HFMM_OK;
 }
 
+// captured body of the preconditioner graph (all launches on stream c)
+static int prec_graph_body(fmm_tree* t, double rtol, int maxit, cudaStream_t c) {
+  fmm_tree_ext* e = ext_of(t);
+  PrecGraph& G = e->pg;
+  const double h = t->h, h2 = h * h, h3 = h2 * h;
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL, G.r_in, h3, nullptr, 0.0, c));
+  HFMM_TRY(fmm_core(t, HFMM_SET_VOL, HFMM_SET_BND, c));
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, t->g_bnd, c));
+  DevOp negV = [t, h2, c](const double2* in, double2* out) -> int {
+    HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, in, -h2, c));
+    HFMM_TRY(fmm_core(t, HFMM_SET_BND, HFMM_SET_BND, c));
+    return fmm_scatter(t, HFMM_SET_BND, nullptr, out, c);
+  };
+  t->skip = G.flags;
+  int st = gmres_cycle_device(e->inner_g, negV, t->g_bnd, t->q_bnd, maxit, rtol, G.flags, G.flags + 1, G.flags + 2, c);
+  t->skip = nullptr;
+  HFMM_TRY(st);
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, G.r_in, h3, t->q_bnd, h2, c));
+  HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, c));
+  return fmm_scatter(t, HFMM_SET_VOL, G.z_out, nullptr, c);
+}
+
+static int prec_graph_build(fmm_tree* t, const double2* r, double2* z, double rtol, int maxit, cudaStream_t s) {
+  fmm_tree_ext* e = ext_of(t);
+  PrecGraph& G = e->pg;
+  prec_graph_drop(G);
+  // one eager apply builds everything the passes create on first use (its
+  // result is the answer of this call; the first replay recomputes it)
+  HFMM_TRY(precond_impl(t, r, z, rtol, maxit, maxit, &G.eager_its, s));
+  if (!G.r_in) {
+    HFMM_TRY(tree_alloc_t(t, &G.r_in, t->n_vol));
+    HFMM_TRY(tree_alloc_t(t, &G.z_out, t->n_vol));
+    HFMM_TRY(tree_alloc_t(t, &G.flags, 4));
+    HFMM_CUDA_TRY(cudaMemsetAsync(G.flags, 0, 4 * sizeof(int), s));
+  }
+  if (!G.cap) HFMM_CUDA_TRY(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+  HFMM_TRY(gmres_work_reserve(e->inner_g, t->n_bnd, maxit, false));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaGraph_t graph = nullptr;
+  HFMM_CUDA_TRY(cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal));
+  t->timer.cap = &G.slots;
+  const int64_t before = launches_so_far();
+  int st = prec_graph_body(t, rtol, maxit, G.cap);
+  t->timer.cap = nullptr;
+  G.kernels = launches_so_far() - before;
+  count_launches(-G.kernels);  // captured, not executed
+  cudaError_t ce = cudaStreamEndCapture(G.cap, &graph);
+  if (st != HFMM_OK || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    prec_graph_drop(G);
+    return st != HFMM_OK ? st : HFMM_ERR_CUDA;
+  }
+  ce = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    G.exec = nullptr;
+    cudaGetLastError();
+    return HFMM_ERR_CUDA;
+  }
+  G.rtol = rtol;
+  G.maxit = maxit;
+  G.timer_mask = t->timer.on ? t->timer.mask : 0;
+  return HFMM_OK;
+}
+
+// z = M^-1 r through the graph (rebuilt when the inner settings or the
+// timed stages change)
+static int precond_graph(fmm_tree* t, const double2* r, double2* z, double rtol, int maxit, cudaStream_t s) {
+  PrecGraph& G = ext_of(t)->pg;
+  const int tmask = t->timer.on ? t->timer.mask : 0;
+  if (G.pending) {  // the previous replay has completed: the caller synchronised since
+    t->timer.resolve_slots(G.slots);
+    G.pending = false;
+  }
+  if (!G.exec || G.rtol != rtol || G.maxit != maxit || G.timer_mask != tmask)
+    HFMM_TRY(prec_graph_build(t, r, z, rtol, maxit, s));
+  HFMM_CUDA_TRY(cudaMemcpyAsync(G.r_in, r, sizeof(double2) * t->n_vol, cudaMemcpyDeviceToDevice, s));
+  HFMM_CUDA_TRY(cudaGraphLaunch(G.exec, s));
+  HFMM_CUDA_TRY(cudaMemcpyAsync(z, G.z_out, sizeof(double2) * t->n_vol, cudaMemcpyDeviceToDevice, s));
+  G.pending = !G.slots.empty();
+  count_launches(G.kernels);
+  return HFMM_OK;
+}
+
 extern "C" int fmm_precond_apply(fmm_tree* t, const void* d_r, void* d_z, double inner_rtol,
                                  int inner_maxit, int inner_m, int* inner_iters, void* stream) {
   if (!t || !d_r || !d_z) return HFMM_ERR_INVALID_ARG;
@@ -304,7 +425,12 @@ extern "C" int gmres_solve(fmm_tree* t, const void* d_b, void* d_x, const hfmm_g
     return st;
   };
   int inner_total = 0;
-  DevOp M = [t, gp, s, &inner_total](const double2* in, double2* out) -> int {
+  const bool graphs = t->use_graphs && gp->inner_m >= gp->inner_maxit;
+  PrecGraph& G = e->pg;
+  if (graphs && G.flags) HFMM_CUDA_TRY(cudaMemsetAsync(G.flags + 2, 0, sizeof(int), s));
+  G.eager_its = 0;
+  DevOp M = [t, gp, s, graphs, &inner_total](const double2* in, double2* out) -> int {
+    if (graphs) return precond_graph(t, in, out, gp->inner_rtol, gp->inner_maxit, s);
     int its = 0;
     int st = precond_impl(t, in, out, gp->inner_rtol, gp->inner_maxit, gp->inner_m, &its, s);
     inner_total += its;
@@ -314,6 +440,21 @@ extern "C" int gmres_solve(fmm_tree* t, const void* d_b, void* d_x, const hfmm_g
   GmresResult R;
   int st = gmres_run(e->outer, A, &M, (const double2*)d_b, (double2*)d_x, gp->restart_m, gp->rtol, maxit,
                      false, true, &R, info ? info->history : nullptr, info ? info->history_len : 0, s);
+  if (graphs && st == HFMM_OK && G.flags) {
+    // inner steps of the graph replays (the first apply ran eagerly when the
+    // graph was built and counted nothing there)
+    int tot = 0;
+    HFMM_CUDA_TRY(cudaMemcpyAsync(&tot, G.flags + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    // the replay that follows an eager build recomputes that apply: its steps
+    // are in `tot` already, so the eager count is not added again
+    inner_total = tot;
+    if (G.pending) {
+      t->timer.resolve_slots(G.slots);
+      G.pending = false;
+    }
+    if (fmm_device_error(s, true)) st = HFMM_ERR_TIMEOUT;
+  }
   if (info) {
     info->iters = R.iters;
     info->restarts = R.restarts;
@@ -344,6 +485,10 @@ extern "C" int fmm_get_stats(const fmm_tree* t, hfmm_stats* st) {
     cudaGetLastError();
   st->ms_last_apply = tt->ms_last_apply;
   tt->timer.flush();
+  if (tt->ext && tt->ext->pg.pending) {
+    tt->timer.resolve_slots(tt->ext->pg.slots);
+    tt->ext->pg.pending = false;
+  }
   st->launches = launches_so_far();
   for (int i = 0; i < HFMM_NSTAGES; ++i) {
     st->stage_ms[i] = tt->timer.ms[i];
@@ -353,9 +498,16 @@ extern "C" int fmm_get_stats(const fmm_tree* t, hfmm_stats* st) {
   return HFMM_OK;
 }
 
-extern "C" int fmm_set_timing(fmm_tree* t, int enable) {
+extern "C" int fmm_use_graphs(fmm_tree* t, int enable) {
   if (!t || (enable != 0 && enable != 1)) return HFMM_ERR_INVALID_ARG;
+  t->use_graphs = enable;
+  return HFMM_OK;
+}
+
+extern "C" int fmm_set_timing(fmm_tree* t, int stage_mask) {
+  if (!t || stage_mask < 0 || stage_mask >= (1 << HFMM_NSTAGES)) return HFMM_ERR_INVALID_ARG;
   t->timer.reset();
-  t->timer.on = enable != 0;
+  t->timer.on = stage_mask != 0;
+  t->timer.mask = stage_mask;
   return HFMM_OK;
 }

@@ -37,7 +37,11 @@ struct FmmDev {
   C<T>* phis;
   int p, P, L;
   T k;
+  const int* skip;  // when set and nonzero, every kernel of the pass returns at once
 };
+
+#define HFMM_SKIP_IF(d) \
+  if ((d).skip && *(d).skip) return
 
 // source/target range of a leaf for a point-set mask
 __device__ __forceinline__ void leaf_range(const int* start, const int* mid, int leaf, int set,
@@ -137,6 +141,7 @@ __device__ void regular_basis_dk_conj(int p, T k, T dx, T dy, T dz, C<T> q, C<T>
 template <typename T, bool DK>
 __global__ void k_p2m(FmmDev<T> d, C<T>* Mout, int64_t leaf_off, int src_set, int chunk, C<T> fac,
                       const int* __restrict__ list) {
+  HFMM_SKIP_IF(d);
   extern __shared__ unsigned char smem_raw[];
   C<T>* basis = reinterpret_cast<C<T>*>(smem_raw);
   const int leaf = list ? list[blockIdx.x] : blockIdx.x;
@@ -198,6 +203,7 @@ __device__ __forceinline__ C<T> matvec_row(const C<T>* Tcol, int ap, const C<T>*
 template <typename T>
 __global__ void k_m2m(FmmDev<T> d, int level, int64_t off_par, int64_t off_child, const C<T>* Min, C<T>* Mout,
                       const C<T>* __restrict__ ops, int src_set, int accumulate, const int* __restrict__ list) {
+  HFMM_SKIP_IF(d);
   extern __shared__ unsigned char smem_raw[];
   C<T>* xs = reinterpret_cast<C<T>*>(smem_raw);  // [8][P]
   __shared__ int has[8];
@@ -241,6 +247,7 @@ __global__ void k_m2m(FmmDev<T> d, int level, int64_t off_par, int64_t off_child
 template <typename T>
 __global__ void k_l2l(FmmDev<T> d, int64_t off_par, int64_t off_child, const C<T>* Lin, C<T>* Lout,
                       const C<T>* __restrict__ ops, int tgt_set, const int* __restrict__ list) {
+  HFMM_SKIP_IF(d);
   extern __shared__ unsigned char smem_raw[];
   C<T>* xs = reinterpret_cast<C<T>*>(smem_raw);
   const int cell = list ? list[blockIdx.x] : blockIdx.x;  // child
@@ -269,6 +276,7 @@ __global__ void k_l2l(FmmDev<T> d, int64_t off_par, int64_t off_child, const C<T
 template <typename T>
 __global__ void k_m2l(FmmDev<T> d, int level, int64_t off, const C<T>* ops, const int* m2l_off,
                       const int* m2l_slot, int m2l_count, int src_set, int tgt_set, int accumulate) {
+  HFMM_SKIP_IF(d);
   extern __shared__ unsigned char smem_raw[];
   C<T>* xs = reinterpret_cast<C<T>*>(smem_raw);
   const int cell = blockIdx.x;
@@ -323,6 +331,7 @@ __global__ void __launch_bounds__(128) k_m2l_tiled(FmmDev<T> d, const int4* __re
                                                    const int* __restrict__ m2l_off,
                                                    const int* __restrict__ m2l_slot, int m2l_count,
                                                    int src_set, int accumulate) {
+  HFMM_SKIP_IF(d);
   constexpr int CT = 8, RT = 16, TC = CT * CM;
   extern __shared__ unsigned char smem_raw[];
   const int P = d.P;
@@ -579,6 +588,7 @@ __global__ void __launch_bounds__(RT * 8) k_m2l_tma(FmmDev<T> d, const int4* __r
                                                     const int* __restrict__ nval_all,
                                                     const C<T>* __restrict__ zero_row,
                                                     C<T>* __restrict__ part, int64_t part_stride, int accumulate) {
+  HFMM_SKIP_IF(d);
   constexpr int CT = 8, TC = CT * CM, NT = RT * CT;
   const int P = d.P;
   const int MS = P + 2;  // padded source row (16-byte multiple, spreads banks)
@@ -729,6 +739,7 @@ __global__ void __launch_bounds__(RT * 8 + 32) k_m2l_ws(FmmDev<T> d, const int4*
                                                         const int* __restrict__ nval_all,
                                                         const C<T>* __restrict__ zero_row,
                                                         C<T>* __restrict__ part, int64_t part_stride, int accumulate) {
+  HFMM_SKIP_IF(d);
   constexpr int CT = 8, TC = CT * CM, NC = RT * CT, NCW = NC / 32;
   const int P = d.P;
   const int MS = P + 2;
@@ -855,6 +866,7 @@ template <typename T>
 __global__ void k_m2l_reduce(FmmDev<T> d, const int4* __restrict__ tiles, const int* __restrict__ cells,
                              const int64_t* __restrict__ level_off, const C<T>* __restrict__ part,
                              int64_t part_stride, int nsplit, int accumulate) {
+  HFMM_SKIP_IF(d);
   const int4 tile = tiles[blockIdx.x];
   const int P = d.P;
   const int64_t off = level_off[tile.x];
@@ -988,6 +1000,7 @@ __global__ void __launch_bounds__(RT * 8) k_m2l_pairs(FmmDev<T> d, const int4* _
                                                       const int64_t* __restrict__ level_off,
                                                       const C<T>* __restrict__ ops, int64_t box_cells,
                                                       C<T>* __restrict__ buf) {
+  HFMM_SKIP_IF(d);
   constexpr int CT = 8, TC = CT * CM;
   const int P = d.P;
   const int MS = P + 2;
@@ -1044,21 +1057,30 @@ __global__ void __launch_bounds__(RT * 8) k_m2l_pairs(FmmDev<T> d, const int4* _
     }
 }
 
-// L of each tile cell = (L +) sum of its pair rows, in its CSR order
+// L of each tile cell = (L +) sum of its pair rows, in its CSR order; one
+// block per (tile, cell), one thread per coefficient (coalesced row reads)
 template <typename T>
 __global__ void k_pairs_reduce(FmmDev<T> d, const int4* __restrict__ tiles, const int* __restrict__ cells,
                                const int64_t* __restrict__ level_off, const int* __restrict__ csr,
                                const C<T>* __restrict__ buf, int accumulate) {
+  HFMM_SKIP_IF(d);
   const int4 tile = tiles[blockIdx.x];
+  const int c = blockIdx.y;
+  if (c >= tile.w) return;
   const int P = d.P;
   const int64_t off = level_off[tile.x];
-  for (int e = threadIdx.x; e < tile.w * P; e += blockDim.x) {
-    int c = e / P, a = e - c * P;
-    int lo = csr[tile.z + c], hi = csr[tile.z + c + 1];
-    C<T> v = mkc<T>(0, 0);
-    for (int q = lo; q < hi; ++q) v = cadd<T>(v, buf[(int64_t)q * P + a]);
-    C<T>* dst = d.Lc + (off + cells[tile.z + c]) * P + a;
-    *dst = accumulate ? cadd<T>(*dst, v) : v;
+  const int lo = csr[tile.z + c], hi = csr[tile.z + c + 1];
+  C<T>* dst = d.Lc + (off + cells[tile.z + c]) * P;
+  for (int a = threadIdx.x; a < P; a += blockDim.x) {
+    C<T> v0 = mkc<T>(0, 0), v1 = mkc<T>(0, 0);
+    int q = lo;
+    for (; q + 1 < hi; q += 2) {  // two independent chains, then combined
+      v0 = cadd<T>(v0, buf[(int64_t)q * P + a]);
+      v1 = cadd<T>(v1, buf[(int64_t)(q + 1) * P + a]);
+    }
+    if (q < hi) v0 = cadd<T>(v0, buf[(int64_t)q * P + a]);
+    C<T> v = cadd<T>(v0, v1);
+    dst[a] = accumulate ? cadd<T>(dst[a], v) : v;
   }
 }
 
@@ -1133,8 +1155,8 @@ int launch_m2l_pairs_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int sr
         d, t->pr_chunks[ci], t->pr_grouped[ci], t->pr_src[ci], t->level_off_dev, ops, t->box_cells, buf);
   }
   if (t->m2l_ntiles[mi] > 0)
-    k_pairs_reduce<T><<<t->m2l_ntiles[mi], 128, 0, s>>>(d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev,
-                                                        t->pr_csr[ci], buf, accumulate);
+    k_pairs_reduce<T><<<dim3(t->m2l_ntiles[mi], t->m2l_tc), 64, 0, s>>>(
+        d, t->m2l_tiles[mi], t->m2l_cells[mi], t->level_off_dev, t->pr_csr[ci], buf, accumulate);
   count_launches(2);
   return hfmm_last_launch();
 }
@@ -1236,6 +1258,7 @@ int launch_m2l_tiled(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, const int
 // phi_i = fac * sum_a L_a R_a(x_i - c)   (forward fac = i k; adjoint fac = 1)
 template <typename T>
 __global__ void k_l2p(FmmDev<T> d, int64_t leaf_off, int tgt_set, C<T> fac, const int* __restrict__ list) {
+  HFMM_SKIP_IF(d);
   extern __shared__ unsigned char smem_raw[];
   C<T>* Ls = reinterpret_cast<C<T>*>(smem_raw);
   const int leaf = list ? list[blockIdx.x] : blockIdx.x;
@@ -1280,6 +1303,7 @@ __global__ void k_l2p(FmmDev<T> d, int64_t leaf_off, int tgt_set, C<T> fac, cons
 template <typename T>
 __global__ void k_l2p_dk(FmmDev<T> d, const C<T>* __restrict__ Lv, const C<T>* __restrict__ Ldv,
                          C<T>* __restrict__ out, int64_t leaf_off, int tgt_set, const int* __restrict__ list) {
+  HFMM_SKIP_IF(d);
   extern __shared__ unsigned char smem_raw[];
   C<T>* Ls = reinterpret_cast<C<T>*>(smem_raw);
   const int leaf = list ? list[blockIdx.x] : blockIdx.x;
@@ -1352,6 +1376,7 @@ struct SrcPt {
 template <typename T>
 __global__ void k_p2p(FmmDev<T> d, const int* near_off, int near_count, int src_set, int tgt_set,
                       double2 sig_vol, double2 sig_bnd) {
+  HFMM_SKIP_IF(d);
   constexpr int TILE = 128;
   __shared__ SrcPt<T> tile[TILE];
   const int leaf = blockIdx.x;
@@ -1476,6 +1501,7 @@ __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restri
                                                 int near_count, int src_set, int tgt_set,
                                                 double2 sig_vol, double2 sig_bnd,
                                                 const int* __restrict__ list) {
+  HFMM_SKIP_IF(d);
   __shared__ StagedSrc<T> spos[W];
   __shared__ C<T> sq[W];
   __shared__ int nb_leaf[128], nb_lo[128], nb_cnt[128], nb_pre[129];
@@ -1635,7 +1661,8 @@ __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restri
 template <typename T>
 __global__ void k_gather(const int64_t* orig, int64_t n_pts, int64_t n_vol, int src_set,
                          const double2* q_vol, double s_vol, const double2* q_bnd, double s_bnd,
-                         C<T>* qs) {
+                         C<T>* qs, const int* skip) {
+  if (skip && *skip) return;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n_pts) return;
   int64_t o = orig[i];
@@ -1654,7 +1681,8 @@ __global__ void k_gather(const int64_t* orig, int64_t n_pts, int64_t n_vol, int 
 
 template <typename T>
 __global__ void k_scatter(const int64_t* pos_of, int64_t n_vol, int64_t n_bnd, int tgt_set,
-                          const C<T>* phis, double2* phi_vol, double2* phi_bnd) {
+                          const C<T>* phis, double2* phi_vol, double2* phi_bnd, const int* skip) {
+  if (skip && *skip) return;
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (o < n_vol) {
     if (tgt_set & HFMM_SET_VOL) {
@@ -1685,6 +1713,7 @@ FmmDev<T> make_dev(fmm_tree* t) {
   d.P = t->P;
   d.L = t->L;
   d.k = T(t->k);
+  d.skip = t->skip;
   return d;
 }
 
@@ -1968,10 +1997,10 @@ int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol,
   t->timer.begin(HFMM_STAGE_GATHER, s);
   if (t->precision == HFMM_FP32)
     k_gather<float><<<g, 256, 0, s>>>(t->orig, t->n_pts, t->n_vol, src_set, q_vol, scale_vol, q_bnd,
-                                      scale_bnd, reinterpret_cast<float2*>(t->qs));
+                                      scale_bnd, reinterpret_cast<float2*>(t->qs), t->skip);
   else
     k_gather<double><<<g, 256, 0, s>>>(t->orig, t->n_pts, t->n_vol, src_set, q_vol, scale_vol, q_bnd,
-                                       scale_bnd, reinterpret_cast<double2*>(t->qs));
+                                       scale_bnd, reinterpret_cast<double2*>(t->qs), t->skip);
   t->timer.end(1, s);
   count_launches(1);
   return hfmm_last_launch();
@@ -2013,10 +2042,10 @@ int fmm_scatter_from(fmm_tree* t, const void* sorted, int tgt_set, double2* phi_
   t->timer.begin(HFMM_STAGE_GATHER, s);
   if (t->precision == HFMM_FP32)
     k_scatter<float><<<g, 256, 0, s>>>(t->pos_of, t->n_vol, t->n_bnd, tgt_set,
-                                       reinterpret_cast<const float2*>(sorted), phi_vol, phi_bnd);
+                                       reinterpret_cast<const float2*>(sorted), phi_vol, phi_bnd, t->skip);
   else
     k_scatter<double><<<g, 256, 0, s>>>(t->pos_of, t->n_vol, t->n_bnd, tgt_set,
-                                        reinterpret_cast<const double2*>(sorted), phi_vol, phi_bnd);
+                                        reinterpret_cast<const double2*>(sorted), phi_vol, phi_bnd, t->skip);
   t->timer.end(1, s);
   count_launches(1);
   return hfmm_last_launch();

@@ -51,7 +51,8 @@ __device__ __forceinline__ double2 block_sum2(double2 v) {
 
 // partial[i * gridDim.x + blk] = sum over the block's share of conj(V_i) w
 __global__ void k_mdot_partial(const double2* __restrict__ V, int64_t ld, int nvec,
-                               const double2* __restrict__ w, int64_t N, double2* partial) {
+                               const double2* __restrict__ w, int64_t N, double2* partial, const int* skip) {
+  if (skip && *skip) return;
   const int i = blockIdx.y;
   const double2* v = V + (int64_t)i * ld;
   double2 acc = make_double2(0, 0);
@@ -64,7 +65,8 @@ __global__ void k_mdot_partial(const double2* __restrict__ V, int64_t ld, int nv
   if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = acc;
 }
 
-__global__ void k_mdot_final(const double2* partial, int nblk, double2* out) {
+__global__ void k_mdot_final(const double2* partial, int nblk, double2* out, const int* skip) {
+  if (skip && *skip) return;
   const int i = blockIdx.x;
   double2 acc = make_double2(0, 0);
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
@@ -76,7 +78,8 @@ __global__ void k_mdot_final(const double2* partial, int nblk, double2* out) {
   if (threadIdx.x == 0) out[i] = acc;
 }
 
-__global__ void k_norm_partial(const double2* __restrict__ x, int64_t N, double* partial) {
+__global__ void k_norm_partial(const double2* __restrict__ x, int64_t N, double* partial, const int* skip) {
+  if (skip && *skip) return;
   double2 acc = make_double2(0, 0);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x) {
     double2 a = x[e];
@@ -86,7 +89,8 @@ __global__ void k_norm_partial(const double2* __restrict__ x, int64_t N, double*
   if (threadIdx.x == 0) partial[blockIdx.x] = acc.x;
 }
 
-__global__ void k_norm_final(const double* partial, int nblk, double* out) {
+__global__ void k_norm_final(const double* partial, int nblk, double* out, const int* skip) {
+  if (skip && *skip) return;
   double2 acc = make_double2(0, 0);
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc.x += partial[b];
   acc = block_sum2(acc);
@@ -95,7 +99,10 @@ __global__ void k_norm_final(const double* partial, int nblk, double* out) {
 
 // w += sign * sum_i coef[i] V_i
 __global__ void k_axpy_multi(const double2* __restrict__ V, int64_t ld, int nvec,
-                             const double2* __restrict__ coef, double sign, double2* w, int64_t N) {
+                             const double2* __restrict__ coef, double sign, double2* w, int64_t N,
+                             const int* skip, const int* nvec_dev) {
+  if (skip && *skip) return;
+  if (nvec_dev) nvec = *nvec_dev;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= N) return;
   double2 acc = w[e];
@@ -113,7 +120,8 @@ __global__ void k_sub(const double2* a, const double2* b, double2* out, int64_t 
 }
 
 // dst = src / *nrm (no-op when the norm is zero)
-__global__ void k_scale_by(const double2* src, const double* nrm, double2* dst, int64_t N) {
+__global__ void k_scale_by(const double2* src, const double* nrm, double2* dst, int64_t N, const int* skip) {
+  if (skip && *skip) return;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double d = *nrm;
   if (e < N && d > 0) dst[e] = make_double2(src[e].x / d, src[e].y / d);
@@ -129,8 +137,9 @@ __global__ void k_cycle_init(int m, const double* beta, double2* g) {
 // scal: [0] ||w|| before orthogonalisation, [1] h_{j+1,j}, [2] relres,
 //       [3] breakdown, [4] ||b||
 __global__ void k_arnoldi(int j, int m, const double2* dots, double2* H, double* cs, double2* sn,
-                          double2* g, double* scal) {
+                          double2* g, double* scal, int* done, int* jdone, double rtol) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (done && *done) return;
   const int ld = m + 1;
   double2* col = H + (int64_t)j * ld;
   for (int i = 0; i <= j; ++i) col[i] = make_double2(dots[i].x + dots[ld + i].x, dots[i].y + dots[ld + i].y);
@@ -167,11 +176,14 @@ __global__ void k_arnoldi(int j, int m, const double2* dots, double2* H, double*
   g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
   g[j] = make_double2(c * gj.x, c * gj.y);
   scal[2] = hypot(g[j + 1].x, g[j + 1].y) / scal[4];
+  if (jdone) *jdone = j + 1;
+  if (done && (scal[2] < rtol || scal[3] != 0.0 || !(scal[2] == scal[2]))) *done = 1;
 }
 
 // y = H(0:k,0:k)^-1 g(0:k), upper triangular
-__global__ void k_backsolve(int kdim, int m, const double2* H, const double2* g, double2* y) {
+__global__ void k_backsolve(int kdim, int m, const double2* H, const double2* g, double2* y, const int* kdim_dev) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (kdim_dev) kdim = *kdim_dev;
   const int ld = m + 1;
   for (int i = kdim - 1; i >= 0; --i) {
     double2 acc = g[i];
@@ -244,16 +256,16 @@ void gmres_work_free(GmresWork& W) {
 }
 
 int dev_norm(GmresWork& W, const double2* x, int64_t N, double* out_dev, cudaStream_t s) {
-  k_norm_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, N, W.partial);
-  k_norm_final<<<1, RED_THREADS, 0, s>>>(W.partial, RED_BLOCKS, out_dev);
+  k_norm_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, N, W.partial, W.skip);
+  k_norm_final<<<1, RED_THREADS, 0, s>>>(W.partial, RED_BLOCKS, out_dev, W.skip);
   count_launches(2);
   return hfmm_last_launch();
 }
 
 static int mdot(GmresWork& W, const double2* V, int nvec, const double2* w, double2* out, cudaStream_t s) {
   dim3 g(RED_BLOCKS, nvec);
-  k_mdot_partial<<<g, RED_THREADS, 0, s>>>(V, W.N, nvec, w, W.N, (double2*)W.partial);
-  k_mdot_final<<<nvec, RED_THREADS, 0, s>>>((double2*)W.partial, RED_BLOCKS, out);
+  k_mdot_partial<<<g, RED_THREADS, 0, s>>>(V, W.N, nvec, w, W.N, (double2*)W.partial, W.skip);
+  k_mdot_final<<<nvec, RED_THREADS, 0, s>>>((double2*)W.partial, RED_BLOCKS, out, W.skip);
   count_launches(2);
   return hfmm_last_launch();
 }
@@ -297,7 +309,7 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
     }
     if (R.iters >= maxit) break;
     k_cycle_init<<<1, 64, 0, s>>>(m, W.scal + 5, W.g);
-    k_scale_by<<<gN, 256, 0, s>>>(W.r, W.scal + 5, W.V, N);
+    k_scale_by<<<gN, 256, 0, s>>>(W.r, W.scal + 5, W.V, N, nullptr);
     count_launches(2);
     int jdone = 0;
     for (int j = 0; j < m; ++j) {
@@ -311,14 +323,14 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
       HFMM_TRY(dev_norm(W, W.w, N, W.scal + 0, s));
       // classical Gram-Schmidt, twice
       HFMM_TRY(mdot(W, W.V, j + 1, W.w, W.dots, s));
-      k_axpy_multi<<<gN, 256, 0, s>>>(W.V, N, j + 1, W.dots, -1.0, W.w, N);
+      k_axpy_multi<<<gN, 256, 0, s>>>(W.V, N, j + 1, W.dots, -1.0, W.w, N, nullptr, nullptr);
       HFMM_TRY(mdot(W, W.V, j + 1, W.w, W.dots + (m + 1), s));
-      k_axpy_multi<<<gN, 256, 0, s>>>(W.V, N, j + 1, W.dots + (m + 1), -1.0, W.w, N);
+      k_axpy_multi<<<gN, 256, 0, s>>>(W.V, N, j + 1, W.dots + (m + 1), -1.0, W.w, N, nullptr, nullptr);
       HFMM_TRY(dev_norm(W, W.w, N, W.scal + 1, s));
-      k_arnoldi<<<1, 1, 0, s>>>(j, m, W.dots, W.H, W.cs, W.sn, W.g, W.scal);
+      k_arnoldi<<<1, 1, 0, s>>>(j, m, W.dots, W.H, W.cs, W.sn, W.g, W.scal, nullptr, nullptr, 0.0);
       count_launches(3);
       if (j + 1 < m) {
-        k_scale_by<<<gN, 256, 0, s>>>(W.w, W.scal + 1, W.V + (int64_t)(j + 1) * N, N);
+        k_scale_by<<<gN, 256, 0, s>>>(W.w, W.scal + 1, W.V + (int64_t)(j + 1) * N, N, nullptr);
         count_launches(1);
       }
       HFMM_TRY(hfmm_last_launch());
@@ -336,8 +348,8 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
         break;
       }
     }
-    k_backsolve<<<1, 1, 0, s>>>(jdone, m, W.H, W.g, W.y);
-    k_axpy_multi<<<gN, 256, 0, s>>>(M ? W.Z : W.V, N, jdone, W.y, 1.0, x, N);
+    k_backsolve<<<1, 1, 0, s>>>(jdone, m, W.H, W.g, W.y, nullptr);
+    k_axpy_multi<<<gN, 256, 0, s>>>(M ? W.Z : W.V, N, jdone, W.y, 1.0, x, N, nullptr, nullptr);
     count_launches(2);
     HFMM_TRY(hfmm_last_launch());
     if (stop) break;
@@ -359,4 +371,61 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
   R.relres_true = W.host[6] / bnorm;
   if (res) *res = R;
   return HFMM_OK;
+}
+
+// ---------------------------------------------------------------- graph form
+
+namespace {
+
+// start of a device-driven cycle: beta = ||b|| (x0 = 0), g = (beta, 0...),
+// done = 1 when b is zero or not finite, jdone = 0
+__global__ void k_cycle_start(int m, double* scal, double2* g, int* done, int* jdone) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double beta = scal[5];
+  scal[4] = beta;
+  for (int i = 0; i <= m; ++i) g[i] = make_double2(i == 0 ? beta : 0.0, 0.0);
+  *done = (beta > 0.0 && beta < 1e300) ? 0 : 1;
+  *jdone = 0;
+}
+
+__global__ void k_count_add(const int* jdone, int* total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *total += *jdone;
+}
+
+}  // namespace
+
+int gmres_cycle_device(GmresWork& W, const DevOp& A, const double2* b, double2* x, int m, double rtol, int* d_done,
+                       int* d_jdone, int* d_total, cudaStream_t s) {
+  const int64_t N = W.N;
+  const unsigned gN = ceil_div(N, 256);
+  if (W.m < m) return HFMM_ERR_INVALID_ARG;
+  HFMM_CUDA_TRY(cudaMemsetAsync(x, 0, N * sizeof(double2), s));
+  W.skip = nullptr;
+  HFMM_TRY(dev_norm(W, b, N, W.scal + 5, s));
+  k_cycle_start<<<1, 1, 0, s>>>(m, W.scal, W.g, d_done, d_jdone);
+  W.skip = d_done;
+  k_scale_by<<<gN, 256, 0, s>>>(b, W.scal + 5, W.V, N, d_done);
+  count_launches(2);
+  for (int j = 0; j < m; ++j) {
+    double2* vj = W.V + (int64_t)j * N;
+    HFMM_TRY(A(vj, W.w));
+    HFMM_TRY(dev_norm(W, W.w, N, W.scal + 0, s));
+    HFMM_TRY(mdot(W, W.V, j + 1, W.w, W.dots, s));
+    k_axpy_multi<<<gN, 256, 0, s>>>(W.V, N, j + 1, W.dots, -1.0, W.w, N, d_done, nullptr);
+    HFMM_TRY(mdot(W, W.V, j + 1, W.w, W.dots + (m + 1), s));
+    k_axpy_multi<<<gN, 256, 0, s>>>(W.V, N, j + 1, W.dots + (m + 1), -1.0, W.w, N, d_done, nullptr);
+    HFMM_TRY(dev_norm(W, W.w, N, W.scal + 1, s));
+    k_arnoldi<<<1, 1, 0, s>>>(j, m, W.dots, W.H, W.cs, W.sn, W.g, W.scal, d_done, d_jdone, rtol);
+    count_launches(3);
+    if (j + 1 < m) {
+      k_scale_by<<<gN, 256, 0, s>>>(W.w, W.scal + 1, W.V + (int64_t)(j + 1) * N, N, d_done);
+      count_launches(1);
+    }
+  }
+  W.skip = nullptr;
+  k_backsolve<<<1, 1, 0, s>>>(0, m, W.H, W.g, W.y, d_jdone);
+  k_axpy_multi<<<gN, 256, 0, s>>>(W.V, N, 0, W.y, 1.0, x, N, nullptr, d_jdone);
+  k_count_add<<<1, 1, 0, s>>>(d_jdone, d_total);
+  count_launches(3);
+  return hfmm_last_launch();
 }

@@ -31,6 +31,7 @@ struct GmresWork {
   double* host = nullptr;    // pinned host mirror of scal
   void* base = nullptr;      // single allocation
   size_t bytes = 0;
+  const int* skip = nullptr; // device flag: reductions return at once when set (graph form)
 };
 
 int gmres_work_reserve(GmresWork& W, int64_t N, int m, bool flexible);
@@ -50,3 +51,11 @@ int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, do
               double* history, int history_len, cudaStream_t s);
 
 int dev_norm(GmresWork& W, const double2* x, int64_t N, double* out_dev, cudaStream_t s);
+
+// One GMRES cycle of m steps from x0 = 0 for capture in a CUDA graph: no
+// host reads; once the device flag *d_done is set (converged or breakdown)
+// the kernels of the remaining steps return at once (the operator's kernels
+// must honour the same flag).  x = V y with y from the first *d_jdone steps;
+// *d_total += *d_jdone.
+int gmres_cycle_device(GmresWork& W, const DevOp& A, const double2* b, double2* x, int m, double rtol, int* d_done,
+                       int* d_jdone, int* d_total, cudaStream_t s);

@@ -20,8 +20,21 @@ int64_t launches_so_far();
 
 // Per-stage CUDA-event timing: pairs of events recorded around each stage's
 // launches, resolved lazily (flush) so that timing adds no synchronisation.
+// While a graph is being captured (`cap` set) each timed stage gets its own
+// pair of external events, recorded at every replay of the graph and
+// resolved after it (resolve_slots).
+struct TimerSlot {
+  int stage;
+  cudaEvent_t a, b;
+  int nlaunch;
+  double work;
+};
+
 struct StageTimer {
   bool on = false;
+  int mask = 0;               // stages timed (bit per stage)
+  bool cur = false;           // the current begin() was recorded
+  std::vector<TimerSlot>* cap = nullptr;
   std::vector<cudaEvent_t> pool;
   std::vector<int> stage_of;  // per recorded pair
   size_t used = 0;            // events used in the pool
@@ -29,7 +42,16 @@ struct StageTimer {
   int64_t launches[HFMM_NSTAGES] = {0};
   double work[HFMM_NSTAGES] = {0};
   void begin(int stage, cudaStream_t s) {
-    if (!on) return;
+    cur = on && ((mask >> stage) & 1);
+    if (!cur) return;
+    if (cap) {
+      TimerSlot sl{stage, nullptr, nullptr, 0, 0.0};
+      cudaEventCreate(&sl.a);
+      cudaEventCreate(&sl.b);
+      cudaEventRecordWithFlags(sl.a, s, cudaEventRecordExternal);
+      cap->push_back(sl);
+      return;
+    }
     if (used + 2 > pool.size()) {
       if (pool.size() >= 8192) flush();
       while (used + 2 > pool.size()) {
@@ -42,11 +64,30 @@ struct StageTimer {
     stage_of.push_back(stage);
   }
   void end(int nlaunch, cudaStream_t s, double w = 0.0) {
-    if (!on) return;
+    if (!cur) return;
+    cur = false;
+    if (cap) {
+      TimerSlot& sl = cap->back();
+      cudaEventRecordWithFlags(sl.b, s, cudaEventRecordExternal);
+      sl.nlaunch = nlaunch;
+      sl.work = w;
+      return;
+    }
     cudaEventRecord(pool[used + 1], s);
     launches[stage_of.back()] += nlaunch;
     work[stage_of.back()] += w;
     used += 2;
+  }
+  void resolve_slots(const std::vector<TimerSlot>& slots) {
+    if (slots.empty()) return;
+    cudaEventSynchronize(slots.back().b);
+    for (const auto& sl : slots) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, sl.a, sl.b) == cudaSuccess) ms[sl.stage] += t;
+      launches[sl.stage] += sl.nlaunch;
+      work[sl.stage] += sl.work;
+    }
+    cudaGetLastError();
   }
   void flush() {
     if (used == 0) return;
@@ -184,6 +225,12 @@ struct fmm_tree {
   void* Lc = nullptr;           // [total_cells][P]
   void* qs = nullptr;           // [n_pts] sorted weights
   void* phis = nullptr;         // [n_pts] sorted potentials
+
+  int use_graphs = 1;           // gmres_solve replays the preconditioner as one CUDA graph
+  // device flag read by every FMM kernel: nonzero = return at once (set while
+  // capturing the graph of the inner solve, whose late iterations are skipped
+  // after convergence); nullptr outside graphs
+  const int* skip = nullptr;
 
   // ---- preconditioner work (complex128)
   double2* g_bnd = nullptr;     // [n_bnd]

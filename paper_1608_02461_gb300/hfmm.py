@@ -88,6 +88,7 @@ SIGNATURES = {
                                            ctypes.POINTER(hfmm_gmres_params),
                                            ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
     "fmm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "fmm_use_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hfmm_direct_sum_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                                ctypes.c_void_p, ctypes.c_void_p]),
@@ -250,8 +251,14 @@ class Tree:
                        info.relres_est, info.relres_true, list(hist[:min(info.iters, history_len)]))
         return x, gi
 
-    def set_timing(self, on: bool):
-        _check(lib().fmm_set_timing(self._h, 1 if on else 0), "fmm_set_timing")
+    def set_timing(self, on=True, stages=None):
+        """Per-stage CUDA-event timing; `stages` = names from STAGES (all when None)."""
+        mask = 0
+        if on:
+            names = STAGES if stages is None else stages
+            for nm in names:
+                mask |= 1 << STAGES.index(nm)
+        _check(lib().fmm_set_timing(self._h, mask), "fmm_set_timing")
 
     def stage_times(self):
         """{stage: (ms, launches, work)} accumulated since set_timing(True);
@@ -259,6 +266,9 @@ class Tree:
         s = self.stats()
         return {name: (s.stage_ms[i], s.stage_launches[i], s.stage_work[i])
                 for i, name in enumerate(STAGES)}
+
+    def use_graphs(self, on: bool):
+        _check(lib().fmm_use_graphs(self._h, 1 if on else 0), "fmm_use_graphs")
 
     def autotune(self, stream=None):
         _check(lib().fmm_autotune(self._h, _stream_ptr(stream)), "fmm_autotune")

@@ -192,3 +192,24 @@ def test_explicit_points_direct_sum():
     # the oracle's FMM on the same points agrees to rounding
     o = ofmm.FMM(pts, N, 8, 0.4, k, 12).apply(q, allm, allm, np.zeros(N))
     assert rel(got, o) < 1e-11
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_preconditioner_equals_host_driven(prec):
+    """The CUDA-graph form of the preconditioner (device-driven inner cycle)
+    reproduces the host-driven form exactly, including early convergence of
+    the inner cycle (inner_rtol reached before inner_maxit)."""
+    n, k = 12, 5.0
+    b = torch.from_numpy(inputs.rhs("uniform_real", n, 9)).to(DEV)
+    for inner_rtol, inner_maxit in [(1e-2, 20), (0.3, 30)]:
+        tg = hfmm.Tree(n, k, 6, 0.4, 16, prec)
+        th = hfmm.Tree(n, k, 6, 0.4, 16, prec)
+        th.use_graphs(False)
+        kw = dict(restart=30, rtol=1e-6, inner_rtol=inner_rtol, inner_maxit=inner_maxit, inner_m=inner_maxit)
+        xg, ig = tg.gmres(b, **kw)
+        xh, ih = th.gmres(b, **kw)
+        assert ig.iters == ih.iters and ig.inner_iters_total == ih.inner_iters_total
+        assert torch.equal(xg, xh)
+        # a second solve replays the captured graph
+        xg2, ig2 = tg.gmres(b, **kw)
+        assert torch.equal(xg2, xh) and ig2.iters == ih.iters
