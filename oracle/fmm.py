@@ -161,7 +161,9 @@ class FMM:
                 t = -np.array(v, dtype=np.float64) * self.w(l)   # c_T - c_S
                 self._m2l_cache[key] = TT.m2l_op(self.p, self.k, t)
             T = self._m2l_cache[key]
-            np.add.at(Lc, t_idx, M[s_idx] @ T.T)
+            # each target appears once per offset, so a plain indexed add is
+            # the sum over the list
+            Lc[t_idx] += M[s_idx] @ T.T
         return Lc
 
     def l2l(self, Lpar, Lchild, l):
