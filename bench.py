@@ -437,7 +437,8 @@ def run_ours(args, world, rank, local):
             "config": {"workload": args.workload, "n": n, "k": w["k"], "p": w["p"], "leaf": w["leaf"],
                        "theta": w["theta"], "restart": w["restart"], "inner_rtol": args.inner_rtol,
                        "inner_maxit": args.inner_maxit,
-                       "fmm_precision": args.precision, "krylov_precision": "fp64",
+                       "fmm_precision": args.precision,
+                       "krylov_precision": ("outer fp64, inner fp32" if args.precision == "fp32" else "fp64"),
                        "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "gmres_iters": info.iters, "inner_iters_total": info.inner_iters_total,

@@ -30,11 +30,21 @@ struct PrecGraph {
 };
 
 struct fmm_tree_ext {
-  GmresWork inner;   // boundary solve V q = -g
+  GmresWork inner;   // boundary solve V q = -g (FP64 form)
   GmresWork inner_g; // the same in the graph form
+  GmresWorkT<float> inner32;    // the complex64 boundary solve of the FP32 form
+  GmresWorkT<float> inner_g32;  // the same in the graph form
   GmresWork outer;   // A x = b
   PrecGraph pg;
 };
+
+// the inner workspaces and boundary vectors of a form
+inline GmresWorkT<double>& inner_ws(fmm_tree_ext* e, double, bool graph) { return graph ? e->inner_g : e->inner; }
+inline GmresWorkT<float>& inner_ws(fmm_tree_ext* e, float, bool graph) { return graph ? e->inner_g32 : e->inner32; }
+inline double2* bnd_g(fmm_tree* t, double) { return t->g_bnd; }
+inline double2* bnd_q(fmm_tree* t, double) { return t->q_bnd; }
+inline float2* bnd_g(fmm_tree* t, float) { return t->g_bnd32; }
+inline float2* bnd_q(fmm_tree* t, float) { return t->q_bnd32; }
 
 static void prec_graph_drop(PrecGraph& G) {
   if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -146,9 +156,15 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   t->m2l_variant = P >= 64 ? 1 : 0;
   if (const char* g = getenv("HFMM_GRAPHS")) t->use_graphs = atoi(g) != 0;
   if (const char* v = getenv("HFMM_M2L_VARIANT")) t->m2l_variant = atoi(v);
+  if (const char* v = getenv("HFMM_LATTICE_P2P")) t->use_lattice_p2p = atoi(v) != 0;
+  if (const char* v = getenv("HFMM_BASIS_TABLE")) t->use_rtab = atoi(v) != 0;
   HFMM_TRY(tree_alloc(t, &t->m2l_part, csz * t->total_cells * P * t->m2l_part_max));
   HFMM_TRY(tree_alloc_t(t, &t->g_bnd, t->n_bnd + 1));
   HFMM_TRY(tree_alloc_t(t, &t->q_bnd, t->n_bnd + 1));
+  if (t->precision == HFMM_FP32) {
+    HFMM_TRY(tree_alloc_t(t, &t->g_bnd32, t->n_bnd + 1));
+    HFMM_TRY(tree_alloc_t(t, &t->q_bnd32, t->n_bnd + 1));
+  }
   HFMM_CUDA_TRY(cudaMemsetAsync(t->M, 0, csz * t->total_cells * P, s));
   HFMM_CUDA_TRY(cudaMemsetAsync(t->Lc, 0, csz * t->total_cells * P, s));
   HFMM_TRY(build_geometry_and_sort(t, d_vol, d_bnd, s));
@@ -158,6 +174,8 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   HFMM_TRY(build_pair_counts(t, s));
   HFMM_TRY(build_m2l_tiles(t, s));
   HFMM_TRY(build_active_lists(t, s));
+  HFMM_TRY(build_lattice_table(t, s));
+  HFMM_TRY(build_basis_table(t, s));
   HFMM_CUDA_TRY(cudaEventCreate(&t->ev0));
   HFMM_CUDA_TRY(cudaEventCreate(&t->ev1));
   HFMM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -235,6 +253,8 @@ extern "C" void fmm_destroy_tree(fmm_tree* tree) {
   fmm_tree_ext* e = ext_of(tree);
   gmres_work_free(e->inner);
   gmres_work_free(e->inner_g);
+  gmres_work_free(e->inner32);
+  gmres_work_free(e->inner_g32);
   gmres_work_free(e->outer);
   prec_graph_drop(e->pg);
   if (e->pg.cap) cudaStreamDestroy(e->pg.cap);
@@ -272,57 +292,78 @@ extern "C" int fmm_apply(fmm_tree* t, int src_set, int tgt_set, const void* d_q_
   return HFMM_OK;
 }
 
-// z = M^-1 r (Sec. 5.2-5.3, homogeneous Dirichlet data)
-static int precond_impl(fmm_tree* t, const double2* r, double2* z, double inner_rtol, int inner_maxit,
-                        int inner_m, int* inner_iters, cudaStream_t s) {
+// z = M^-1 r (Sec. 5.2-5.3, homogeneous Dirichlet data).  The inner solve
+// runs on complex vectors of real type R: the precision of the FMM form.
+template <typename R>
+static int precond_impl_t(fmm_tree* t, const double2* r, double2* z, double inner_rtol, int inner_maxit,
+                          int inner_m, int* inner_iters, cudaStream_t s) {
   const double h = t->h, h2 = h * h, h3 = h2 * h;
-  // Pass A: g = G_{Gamma,Omega} (h^3 r)
-  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL, r, h3, nullptr, 0.0, s));
-  HFMM_TRY(fmm_core(t, HFMM_SET_VOL, HFMM_SET_BND, s));
-  HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, t->g_bnd, s));
-  // inner solve V q = -g; V x = h^2 G_{Gamma,Gamma} x + s_Gamma x (Pass B)
   fmm_tree_ext* e = ext_of(t);
-  HFMM_TRY(gmres_work_reserve(e->inner, t->n_bnd, inner_m, false));
-  // rhs = -g, computed in place with a scaled gather/scatter-free kernel: reuse
-  // GMRES on the negated operator instead: solve (-V) q = g
-  DevOp negV = [t, h2, s](const double2* in, double2* out) -> int {
+  GmresWorkT<R>& W = inner_ws(e, R(0), false);
+  C<R>* g = bnd_g(t, R(0));
+  C<R>* q = bnd_q(t, R(0));
+  const double2* none = nullptr;
+  // Pass A: g = G_{Gamma,Omega} (h^3 r)
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL, r, h3, none, 0.0, s));
+  HFMM_TRY(fmm_core(t, HFMM_SET_VOL, HFMM_SET_BND, s));
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, g, s));
+  // inner solve V q = -g with V x = h^2 G_{Gamma,Gamma} x + s_Gamma x (Pass B),
+  // written as (-V) q = g
+  HFMM_TRY(gmres_work_reserve(W, t->n_bnd, inner_m, false));
+  DevOpT<R> negV = [t, h2, s](const C<R>* in, C<R>* out) -> int {
     HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, in, -h2, s));
     HFMM_TRY(fmm_core(t, HFMM_SET_BND, HFMM_SET_BND, s));
     return fmm_scatter(t, HFMM_SET_BND, nullptr, out, s);
   };
-  HFMM_CUDA_TRY(cudaMemsetAsync(t->q_bnd, 0, sizeof(double2) * t->n_bnd, s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(C<R>) * t->n_bnd, s));
   GmresResult ir;
-  HFMM_TRY(gmres_run(e->inner, negV, nullptr, t->g_bnd, t->q_bnd, inner_m, inner_rtol, inner_maxit,
-                     true, false, &ir, nullptr, 0, s));
+  HFMM_TRY(gmres_run<R>(W, negV, nullptr, g, q, inner_m, inner_rtol, inner_maxit, true, false, &ir, nullptr, 0, s));
   if (inner_iters) *inner_iters = ir.iters;
   // Pass C: z = G_{Omega,Omega} (h^3 r) + G_{Omega,Gamma} (h^2 q) + s_Omega r
-  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, r, h3, t->q_bnd, h2, s));
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, r, h3, q, h2, s));
   HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, s));
-  HFMM_TRY(fmm_scatter(t, HFMM_SET_VOL, z, nullptr, s));
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_VOL, z, (C<R>*)nullptr, s));
   if (fmm_device_error(s, true)) return HFMM_ERR_TIMEOUT;
   return HFMM_OK;
 }
 
+static int precond_impl(fmm_tree* t, const double2* r, double2* z, double inner_rtol, int inner_maxit,
+                        int inner_m, int* inner_iters, cudaStream_t s) {
+  if (t->precision == HFMM_FP32)
+    return precond_impl_t<float>(t, r, z, inner_rtol, inner_maxit, inner_m, inner_iters, s);
+  return precond_impl_t<double>(t, r, z, inner_rtol, inner_maxit, inner_m, inner_iters, s);
+}
+
 // captured body of the preconditioner graph (all launches on stream c)
-static int prec_graph_body(fmm_tree* t, double rtol, int maxit, cudaStream_t c) {
+template <typename R>
+static int prec_graph_body_t(fmm_tree* t, double rtol, int maxit, cudaStream_t c) {
   fmm_tree_ext* e = ext_of(t);
   PrecGraph& G = e->pg;
+  GmresWorkT<R>& W = inner_ws(e, R(0), true);
+  C<R>* g = bnd_g(t, R(0));
+  C<R>* q = bnd_q(t, R(0));
+  const double2* none = nullptr;
   const double h = t->h, h2 = h * h, h3 = h2 * h;
-  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL, G.r_in, h3, nullptr, 0.0, c));
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL, G.r_in, h3, none, 0.0, c));
   HFMM_TRY(fmm_core(t, HFMM_SET_VOL, HFMM_SET_BND, c));
-  HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, t->g_bnd, c));
-  DevOp negV = [t, h2, c](const double2* in, double2* out) -> int {
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, g, c));
+  DevOpT<R> negV = [t, h2, c](const C<R>* in, C<R>* out) -> int {
     HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, in, -h2, c));
     HFMM_TRY(fmm_core(t, HFMM_SET_BND, HFMM_SET_BND, c));
     return fmm_scatter(t, HFMM_SET_BND, nullptr, out, c);
   };
   t->skip = G.flags;
-  int st = gmres_cycle_device(e->inner_g, negV, t->g_bnd, t->q_bnd, maxit, rtol, G.flags, G.flags + 1, G.flags + 2, c);
+  int st = gmres_cycle_device<R>(W, negV, g, q, maxit, rtol, G.flags, G.flags + 1, G.flags + 2, c);
   t->skip = nullptr;
   HFMM_TRY(st);
-  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, G.r_in, h3, t->q_bnd, h2, c));
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, G.r_in, h3, q, h2, c));
   HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, c));
-  return fmm_scatter(t, HFMM_SET_VOL, G.z_out, nullptr, c);
+  return fmm_scatter(t, HFMM_SET_VOL, G.z_out, (C<R>*)nullptr, c);
+}
+
+static int prec_graph_body(fmm_tree* t, double rtol, int maxit, cudaStream_t c) {
+  if (t->precision == HFMM_FP32) return prec_graph_body_t<float>(t, rtol, maxit, c);
+  return prec_graph_body_t<double>(t, rtol, maxit, c);
 }
 
 static int prec_graph_build(fmm_tree* t, const double2* r, double2* z, double rtol, int maxit, cudaStream_t s) {
@@ -339,7 +380,10 @@ static int prec_graph_build(fmm_tree* t, const double2* r, double2* z, double rt
     HFMM_CUDA_TRY(cudaMemsetAsync(G.flags, 0, 4 * sizeof(int), s));
   }
   if (!G.cap) HFMM_CUDA_TRY(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
-  HFMM_TRY(gmres_work_reserve(e->inner_g, t->n_bnd, maxit, false));
+  if (t->precision == HFMM_FP32)
+    HFMM_TRY(gmres_work_reserve(e->inner_g32, t->n_bnd, maxit, false));
+  else
+    HFMM_TRY(gmres_work_reserve(e->inner_g, t->n_bnd, maxit, false));
   HFMM_CUDA_TRY(cudaStreamSynchronize(s));
   cudaGraph_t graph = nullptr;
   HFMM_CUDA_TRY(cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal));

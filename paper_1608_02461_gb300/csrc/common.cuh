@@ -8,6 +8,11 @@
 
 #define HFMM_MAX_P 16
 #define HFMM_MAX_LEVEL 9
+// lattice near-field kernel: sources staged per window, and the largest
+// table it stages in shared memory (table + window + 4 KB within 227 KB)
+#define HFMM_LAT_WS 2048
+#define HFMM_SMEM_MAX (227 * 1024)
+#define HFMM_LAT_TABLE_MAX_BYTES (180 * 1024)
 
 // ---------------------------------------------------------------- complex
 

@@ -9,6 +9,9 @@
 // Kernels are templated on the arithmetic type T (double: plain FP64 form;
 // float: FP32 form with complex numbers as float pairs).
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "special.cuh"
 #include "tree.cuh"
@@ -182,6 +185,110 @@ __global__ void k_p2m(FmmDev<T> d, C<T>* Mout, int64_t leaf_off, int src_set, in
   for (int s = 0; s < 4; ++s) {
     int a = threadIdx.x + s * blockDim.x;
     if (a < P) M[a] = acc[s];
+  }
+}
+
+// Regular basis table: row i holds R_a(x_i - c) (a < P) for every sorted
+// point i and the centre c of its leaf, evaluated in FP64 once per tree and
+// stored in the precision of the form.  P2M and L2P then reduce to short
+// complex dot products over the rows (no special functions per apply).
+template <typename T>
+__global__ void k_basis_table(const double* __restrict__ xyz, const int* __restrict__ leaf_start, int L, int p,
+                              double k, C<T>* __restrict__ R) {
+  const int leaf = blockIdx.x;
+  const int P = p * p;
+  int ix, iy, iz;
+  morton_decode((uint64_t)leaf, ix, iy, iz);
+  const double w = ldexp(1.0, -L);
+  for (int i = leaf_start[leaf] + threadIdx.x; i < leaf_start[leaf + 1]; i += blockDim.x) {
+    const double dx = xyz[3 * (int64_t)i] - (ix + 0.5) * w;
+    const double dy = xyz[3 * (int64_t)i + 1] - (iy + 0.5) * w;
+    const double dz = xyz[3 * (int64_t)i + 2] - (iz + 0.5) * w;
+    double r, ct, st, cp, sp;
+    direction<double>(dx, dy, dz, r, ct, st, cp, sp);
+    double jn[HFMM_MAX_P];
+    double pl[HFMM_MAX_P * (HFMM_MAX_P + 1) / 2];
+    sph_bessel_j<double>(k * r, p, jn);
+    legendre_bar<double>(ct, st, p, pl);
+    C<T>* out = R + (int64_t)i * P;
+    double er = 1.0, ei = 0.0;  // e^{i m phi}
+    for (int m = 0; m < p; ++m) {
+      for (int n = m; n < p; ++n) {
+        const double v = jn[n] * pl[n * (n + 1) / 2 + m];
+        const double Rx = v * er, Ry = v * ei;  // R_{n,m}
+        out[n * n + n + m] = mkc<T>(T(Rx), T(Ry));
+        if (m > 0) {  // R_{n,-m} = (-1)^m conj(R_{n,m})
+          const double sg = (m & 1) ? -1.0 : 1.0;
+          out[n * n + n - m] = mkc<T>(T(sg * Rx), T(-sg * Ry));
+        }
+      }
+      const double nr = er * cp - ei * sp, ni = er * sp + ei * cp;
+      er = nr;
+      ei = ni;
+    }
+  }
+}
+
+// M_a(leaf) = fac sum_i conj(R_ia) q_i over the leaf's points of src_set
+template <typename T>
+__global__ void __launch_bounds__(64) k_p2m_tab(FmmDev<T> d, const C<T>* __restrict__ R, C<T>* Mout,
+                                                int64_t leaf_off, int src_set, C<T> fac,
+                                                const int* __restrict__ list) {
+  HFMM_SKIP_IF(d);
+  __shared__ C<T> qsh[64];
+  const int leaf = list ? list[blockIdx.x] : blockIdx.x;
+  const int P = d.P;
+  C<T>* M = Mout + (leaf_off + leaf) * P;
+  int lo, hi;
+  leaf_range(d.leaf_start, d.leaf_mid, leaf, src_set, lo, hi);
+  for (int a0 = 0; a0 < P; a0 += 64) {
+    const int a = a0 + threadIdx.x;
+    C<T> acc = mkc<T>(0, 0);
+    for (int base = lo; base < hi; base += 64) {
+      const int nb = min(64, hi - base);
+      __syncthreads();
+      if ((int)threadIdx.x < nb) qsh[threadIdx.x] = d.qs[base + threadIdx.x];
+      __syncthreads();
+      if (a < P) {
+        const C<T>* Rc = R + (int64_t)base * P + a;
+#pragma unroll 8
+        for (int jj = 0; jj < nb; ++jj) cfma_conj<T>(acc, Rc[(int64_t)jj * P], qsh[jj]);
+      }
+    }
+    if (a < P) M[a] = cmul<T>(fac, acc);
+  }
+}
+
+// phi_i = fac sum_a L_a R_ia over the leaf's points of tgt_set; eight lanes
+// per point, each a strided share of the coefficients
+template <typename T>
+__global__ void __launch_bounds__(256) k_l2p_tab(FmmDev<T> d, const C<T>* __restrict__ R, int64_t leaf_off,
+                                                 int tgt_set, C<T> fac, const int* __restrict__ list) {
+  HFMM_SKIP_IF(d);
+  extern __shared__ unsigned char smem_raw[];
+  C<T>* Ls = reinterpret_cast<C<T>*>(smem_raw);
+  const int leaf = list ? list[blockIdx.x] : blockIdx.x;
+  const int P = d.P;
+  int lo, hi;
+  leaf_range(d.leaf_start, d.leaf_mid, leaf, tgt_set, lo, hi);
+  if (hi <= lo) return;
+  for (int e = threadIdx.x; e < P; e += blockDim.x) Ls[e] = d.Lc[(leaf_off + leaf) * P + e];
+  __syncthreads();
+  const int sub = threadIdx.x & 7, grp = threadIdx.x >> 3;
+  for (int ib = lo; ib < hi; ib += 32) {
+    const int i = ib + grp;
+    const bool act = i < hi;
+    C<T> acc = mkc<T>(0, 0);
+    if (act) {
+      const C<T>* Ri = R + (int64_t)i * P;
+      for (int a = sub; a < P; a += 8) cfma<T>(acc, Ls[a], Ri[a]);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (act && sub == 0) d.phis[i] = cmul<T>(fac, acc);
   }
 }
 
@@ -1656,45 +1763,236 @@ __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restri
   }
 }
 
-// ---------------------------------------------------------------- gather / scatter
+// P2P on lattice trees.  Every point is a node of h Z^3, so the kernel
+// between a target and a source depends only on their integer offset d.
+// With lin = (iz W + iy) W + ix (W = 2D + 1, D the largest offset component
+// between near leaves) the offset is coded by delta = lin_t - lin_s, a
+// bijection of [-D, D]^3 onto [-(W^3-1)/2, (W^3-1)/2] with -d <-> -delta;
+// G(d) = G(-d), so the entry of the pair is tab[|delta|].  The half table is
+// staged once per block in shared memory with bulk copies; blocks are
+// persistent (two per SM in FP32, so that one block's leaf setup overlaps the
+// other's sums) and take target leaves in turn.  Per pair: one broadcast read
+// of the staged source {q, lin}, one table read and a complex multiply-add;
+// no transcendental functions.  As in k_p2p_v2, each target is served by tpt
+// threads summing strided shares of a window of staged sources (consecutive
+// sources of a leaf are consecutive lattice nodes, so the table reads of a
+// warp fall in distinct banks); FP32 window sums are added with Kahan
+// compensation.  KMODE 0: G; 1: conj(G) (adjoint).
+template <typename T> struct LatSrc;
+template <> struct LatSrc<float> { float4 v; };                       // q.x, q.y, lin (bits), 0
+template <> struct LatSrc<double> { double2 q; int lin; int pad[3]; };
 
-template <typename T>
-__global__ void k_gather(const int64_t* orig, int64_t n_pts, int64_t n_vol, int src_set,
-                         const double2* q_vol, double s_vol, const double2* q_bnd, double s_bnd,
-                         C<T>* qs, const int* skip) {
-  if (skip && *skip) return;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n_pts) return;
-  int64_t o = orig[i];
-  double2 v = make_double2(0, 0);
-  if (o < n_vol) {
-    if (src_set & HFMM_SET_VOL) {
-      double2 q = q_vol[o];
-      v = make_double2(q.x * s_vol, q.y * s_vol);
-    }
-  } else if (src_set & HFMM_SET_BND) {
-    double2 q = q_bnd[o - n_vol];
-    v = make_double2(q.x * s_bnd, q.y * s_bnd);
-  }
-  qs[i] = mkc<T>(T(v.x), T(v.y));
+constexpr int LAT_THREADS = 512;
+constexpr int LAT_WS = HFMM_LAT_WS;  // staged sources per window
+
+__device__ __forceinline__ void lat_stage(LatSrc<float>& o, float2 q, int l) {
+  o.v = make_float4(q.x, q.y, __int_as_float(l), 0.f);
+}
+__device__ __forceinline__ void lat_stage(LatSrc<double>& o, double2 q, int l) {
+  o.q = q;
+  o.lin = l;
+}
+__device__ __forceinline__ void lat_read(const LatSrc<float>& o, float2& q, int& l) {
+  const float4 v = o.v;
+  q = make_float2(v.x, v.y);
+  l = __float_as_int(v.z);
+}
+__device__ __forceinline__ void lat_read(const LatSrc<double>& o, double2& q, int& l) {
+  q = o.q;
+  l = o.lin;
 }
 
-template <typename T>
-__global__ void k_scatter(const int64_t* pos_of, int64_t n_vol, int64_t n_bnd, int tgt_set,
-                          const C<T>* phis, double2* phi_vol, double2* phi_bnd, const int* skip) {
-  if (skip && *skip) return;
-  int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (o < n_vol) {
-    if (tgt_set & HFMM_SET_VOL) {
-      C<T> v = phis[pos_of[o]];
-      phi_vol[o] = make_double2((double)v.x, (double)v.y);
+template <typename T, int KMODE>
+__global__ void __launch_bounds__(LAT_THREADS, sizeof(T) == 4 ? 2 : 1)
+    k_p2p_lat(FmmDev<T> d, const int* __restrict__ near_off, int near_count, int src_set, int tgt_set,
+              double2 sig_vol, double2 sig_bnd, const int* __restrict__ list, int nlist,
+              const C<T>* __restrict__ tab, uint32_t tab_bytes, const int* __restrict__ lin) {
+  HFMM_SKIP_IF(d);
+  extern __shared__ __align__(128) unsigned char lat_smem[];
+  const C<T>* stab = reinterpret_cast<const C<T>*>(lat_smem);
+  LatSrc<T>* ssrc = reinterpret_cast<LatSrc<T>*>(lat_smem + tab_bytes);
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int q_lo[128], q_cnt[128];
+  __shared__ int nb_lo[128], nb_pre[129];
+  __shared__ int n_nb;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(&bar, tab_bytes);
+    constexpr uint32_t CH = 32768;
+    for (uint32_t off = 0; off < tab_bytes; off += CH)
+      bulk_copy_g2s(lat_smem + off, reinterpret_cast<const unsigned char*>(tab) + off,
+                    tab_bytes - off < CH ? tab_bytes - off : CH, &bar);
+  }
+  const bool ok = mbar_wait_bounded(&bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      atomicExch(&g_fmm_error, HFMM_ERR_TIMEOUT);
+      mbar_wait_bounded(&bar, 0);
     }
-  } else if (o < n_vol + n_bnd) {
-    if (tgt_set & HFMM_SET_BND) {
-      C<T> v = phis[pos_of[o]];
-      phi_bnd[o - n_vol] = make_double2((double)v.x, (double)v.y);
+    __syncthreads();
+    return;
+  }
+  const int s = 1 << d.L;
+  for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+    const int leaf = list[li];
+    int tlo, thi;
+    leaf_range(d.leaf_start, d.leaf_mid, leaf, tgt_set, tlo, thi);
+    const int ntgt = thi - tlo;
+    if (ntgt <= 0) continue;  // uniform over the block
+    int ix, iy, iz;
+    morton_decode((uint64_t)leaf, ix, iy, iz);
+    __syncthreads();  // the previous leaf is done with the lists and the window
+    // source ranges of the near leaves, one offset per thread
+    for (int q = tid; q < near_count; q += LAT_THREADS) {
+      int cnt = 0, lo = 0;
+      const int o = near_off[q];
+      const int jx = ix + (o & 255) - 128, jy = iy + ((o >> 8) & 255) - 128, jz = iz + ((o >> 16) & 255) - 128;
+      if (jx >= 0 && jy >= 0 && jz >= 0 && jx < s && jy < s && jz < s) {
+        int hi;
+        leaf_range(d.leaf_start, d.leaf_mid, (int)morton_encode(jx, jy, jz), src_set, lo, hi);
+        cnt = hi > lo ? hi - lo : 0;
+      }
+      q_lo[q] = lo;
+      q_cnt[q] = cnt;
+    }
+    __syncthreads();
+    // compaction and prefix sums of the non-empty ones (warp 0)
+    if (warp == 0) {
+      int base = 0, run = 0;
+      for (int c0 = 0; c0 < near_count; c0 += 32) {
+        const int q = c0 + lane;
+        const int cnt = q < near_count ? q_cnt[q] : 0;
+        const unsigned has = __ballot_sync(0xffffffffu, cnt > 0);
+        int v = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += u;
+        }
+        const int pos = base + __popc(has & ((1u << lane) - 1u));
+        if (cnt > 0) {
+          nb_lo[pos] = q_lo[q];
+          nb_pre[pos + 1] = run + v;
+        }
+        run += __shfl_sync(0xffffffffu, v, 31);
+        base += __popc(has);
+      }
+      if (lane == 0) {
+        nb_pre[0] = 0;
+        n_nb = base;
+      }
+    }
+    __syncthreads();
+    const int nnb = n_nb;
+    const int total = nb_pre[nnb];
+    int tpt = 1;
+    while (tpt < 32 && (tpt * 2) * ntgt <= LAT_THREADS) tpt *= 2;
+    const int tslots = LAT_THREADS / tpt;
+    const int sub = tid & (tpt - 1);
+    for (int tb = 0; tb < ntgt; tb += tslots) {
+      const int ti = tb + tid / tpt;
+      const bool active = ti < ntgt;
+      const int i = tlo + (active ? ti : 0);
+      const int lt = lin[i];
+      C<T> tot = mkc<T>(0, 0), comp = mkc<T>(0, 0);
+      for (int wb = 0; wb < total; wb += LAT_WS) {
+        const int wn = min(LAT_WS, total - wb);
+        __syncthreads();
+        for (int e = tid; e < wn; e += LAT_THREADS) {
+          const int g = wb + e;
+          int lo = 0, hi = nnb;  // near leaf of staged source g: last q with nb_pre[q] <= g
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (nb_pre[mid] <= g) lo = mid;
+            else hi = mid;
+          }
+          const int j = nb_lo[lo] + (g - nb_pre[lo]);
+          lat_stage(ssrc[e], d.qs[j], lin[j]);
+        }
+        __syncthreads();
+        C<T> part = mkc<T>(0, 0);
+        if (active) {
+#pragma unroll 8
+          for (int e = sub; e < wn; e += tpt) {
+            C<T> q;
+            int ls;
+            lat_read(ssrc[e], q, ls);
+            const C<T> g = stab[abs(lt - ls)];
+            if constexpr (KMODE == 0) {
+              part.x = fma(g.x, q.x, fma(-g.y, q.y, part.x));
+              part.y = fma(g.x, q.y, fma(g.y, q.x, part.y));
+            } else {
+              part.x = fma(g.x, q.x, fma(g.y, q.y, part.x));
+              part.y = fma(g.x, q.y, fma(-g.y, q.x, part.y));
+            }
+          }
+        }
+        if constexpr (sizeof(T) == 4) {
+          const T yx = part.x - comp.x, yy = part.y - comp.y;
+          const T tx = tot.x + yx, ty = tot.y + yy;
+          comp.x = (tx - tot.x) - yx;
+          comp.y = (ty - tot.y) - yy;
+          tot.x = tx;
+          tot.y = ty;
+        } else {
+          tot = cadd<T>(tot, part);
+        }
+      }
+      for (int o = tpt >> 1; o > 0; o >>= 1) {
+        tot.x += __shfl_xor_sync(0xffffffffu, tot.x, o);
+        tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
+      }
+      if (active && sub == 0) {
+        const bool is_vol = i < d.leaf_mid[leaf];
+        if ((is_vol && (src_set & HFMM_SET_VOL)) || (!is_vol && (src_set & HFMM_SET_BND))) {
+          const double2 sg = is_vol ? sig_vol : sig_bnd;  // conjugated by the caller in adjoint mode
+          cfma<T>(tot, mkc<T>(T(sg.x), T(sg.y)), d.qs[i]);
+        }
+        d.phis[i] = cadd<T>(d.phis[i], tot);
+      }
     }
   }
+}
+
+// ---------------------------------------------------------------- gather / scatter
+
+// qs[pos(o)] = scale q[o] for the original indices o of the point sets in
+// `src_set` (points outside the set keep stale values: no kernel reads them);
+// the boundary vector is complex128 or complex64 (QB)
+template <typename T, typename QB>
+__global__ void k_gather(const int64_t* __restrict__ pos_of, int64_t o0, int64_t o1, int64_t n_vol,
+                         const double2* __restrict__ q_vol, double s_vol, const QB* __restrict__ q_bnd,
+                         double s_bnd, C<T>* qs, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t o = o0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= o1) return;
+  C<T> v;
+  if (o < n_vol) {
+    const double2 q = q_vol[o];
+    v = mkc<T>(T(q.x * s_vol), T(q.y * s_vol));
+  } else {
+    const QB q = q_bnd[o - n_vol];
+    v = mkc<T>(T(q.x * s_bnd), T(q.y * s_bnd));
+  }
+  qs[pos_of[o]] = v;
+}
+
+// out[o] = phis[pos(o)] for the original indices o of `tgt_set`
+template <typename T, typename OB>
+__global__ void k_scatter(const int64_t* __restrict__ pos_of, int64_t o0, int64_t o1, int64_t n_vol,
+                          const C<T>* __restrict__ phis, double2* phi_vol, OB* phi_bnd, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t o = o0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= o1) return;
+  const C<T> v = phis[pos_of[o]];
+  if (o < n_vol)
+    phi_vol[o] = make_double2((double)v.x, (double)v.y);
+  else
+    phi_bnd[o - n_vol] = mkc<decltype(phi_bnd->x)>(v.x, v.y);
 }
 
 template <typename T>
@@ -1723,10 +2021,22 @@ int threads_for(int P) {  // four threads per expansion coefficient (M2M / L2L)
   return th;
 }
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`.  The
+// limit is process-wide state of the function, and handles driven from
+// several host threads (batched solves) launch the same kernel with
+// different sizes, so it is only ever raised (under a lock), never lowered.
 template <typename T>
 int set_smem(const void* fn, size_t bytes) {
-  if (bytes > 48 * 1024)
-    HFMM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  if (bytes <= 48 * 1024) return HFMM_OK;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  HFMM_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{dev, fn}];
+  if (cur >= bytes) return HFMM_OK;
+  HFMM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
   return HFMM_OK;
 }
 
@@ -1765,10 +2075,80 @@ int m2l_stage(fmm_tree* t, const FmmDev<T>& d, const C<T>* m2l, int src_set, int
   return hfmm_last_launch();
 }
 
+static int sm_count() {
+  static int c = 0;
+  if (!c) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    c = v > 0 ? v : 1;
+  }
+  return c;
+}
+
+template <typename T>
+int launch_p2m(fmm_tree* t, const FmmDev<T>& d, C<T>* Mout, int src_set, C<T> fac, cudaStream_t s) {
+  const int L = t->L, P = t->P;
+  const int na = act_n(t, src_set, L);
+  if (!na) return HFMM_OK;
+  if (t->rtab && t->use_rtab) {
+    k_p2m_tab<T><<<na, 64, 0, s>>>(d, reinterpret_cast<const C<T>*>(t->rtab), Mout, t->level_off[L], src_set, fac,
+                                   act_list(t, src_set, L));
+    return hfmm_last_launch();
+  }
+  const int chunk = 32;
+  const size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
+  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
+  k_p2m<T, false><<<na, 64, sm_p2m, s>>>(d, Mout, t->level_off[L], src_set, chunk, fac, act_list(t, src_set, L));
+  return hfmm_last_launch();
+}
+
+template <typename T>
+int launch_l2p(fmm_tree* t, const FmmDev<T>& d, int tgt_set, C<T> fac, cudaStream_t s) {
+  const int L = t->L, P = t->P;
+  const int na = act_n(t, tgt_set, L);
+  if (!na) return HFMM_OK;
+  const size_t sm1 = (size_t)P * sizeof(C<T>);
+  if (t->rtab && t->use_rtab) {
+    k_l2p_tab<T><<<na, 256, sm1, s>>>(d, reinterpret_cast<const C<T>*>(t->rtab), t->level_off[L], tgt_set, fac,
+                                      act_list(t, tgt_set, L));
+    return hfmm_last_launch();
+  }
+  k_l2p<T><<<na, 64, sm1, s>>>(d, t->level_off[L], tgt_set, fac, act_list(t, tgt_set, L));
+  return hfmm_last_launch();
+}
+
+template <typename T, int KMODE>
+int launch_p2p_lat(fmm_tree* t, const FmmDev<T>& d, int src_set, int tgt_set, double2 sv, double2 sb,
+                   cudaStream_t s) {
+  const int na = act_n(t, tgt_set, t->L);
+  if (!na) return HFMM_OK;
+  const int64_t nh = t->lat_half;  // half-table entries, padded to 16 bytes
+  const uint32_t tab_bytes = (uint32_t)(nh * sizeof(C<T>));
+  const size_t smem = tab_bytes + (size_t)LAT_WS * sizeof(LatSrc<T>);
+  auto kern = k_p2p_lat<T, KMODE>;
+  HFMM_TRY(set_smem<T>((const void*)kern, smem));
+  int per_sm = 0;
+  HFMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LAT_THREADS, smem));
+  if (per_sm < 1) return HFMM_ERR_UNSUPPORTED;
+  const int grid = std::min(na, per_sm * sm_count());
+  kern<<<grid, LAT_THREADS, smem, s>>>(d, t->near_off, t->near_count, src_set, tgt_set, sv, sb,
+                                       act_list(t, tgt_set, t->L), na,
+                                       reinterpret_cast<const C<T>*>(sizeof(T) == 4 ? (const void*)t->lat_tab32
+                                                                                    : (const void*)t->lat_tab64),
+                                       tab_bytes, t->lat_lin);
+  return hfmm_last_launch();
+}
+
 template <typename T, int KMODE>
 int p2p_stage(fmm_tree* t, const FmmDev<T>& d, int src_set, int tgt_set, double2 sv, double2 sb,
               cudaStream_t s) {
   const int nleaf = 1 << (3 * t->L);
+  if constexpr (KMODE != 2) {
+    if (t->lat_D > 0 && t->use_lattice_p2p && t->near_count <= 128 &&
+        (sizeof(T) == 4 || t->lat_tab64_fits))
+      return launch_p2p_lat<T, KMODE>(t, d, src_set, tgt_set, sv, sb, s);
+  }
   if (t->near_count <= 128) {
     const int na = act_n(t, tgt_set, t->L);
     if (na)
@@ -1808,11 +2188,7 @@ int core_adjoint_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   C<T>* Lh = d.Lc;  // cotangents of the local expansions
   C<T>* Mh = d.M;   // cotangents of the multipole expansions
   const int Sp = tgt_set, Tp = src_set;
-  const int chunk = 32;
-  size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
-  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
-  if (act_n(t, Sp, L))
-    k_p2m<T, false><<<act_n(t, Sp, L), 64, sm_p2m, s>>>(d, Lh, t->level_off[L], Sp, chunk, mkc<T>(0, -d.k), act_list(t, Sp, L));
+  HFMM_TRY(launch_p2m<T>(t, d, Lh, Sp, mkc<T>(0, -d.k), s));
   size_t sm8 = 8 * (size_t)P * sizeof(C<T>);
   HFMM_TRY(set_smem<T>((const void*)k_m2m<T>, sm8));
   for (int l = L - 1; l >= 2; --l)
@@ -1831,8 +2207,7 @@ int core_adjoint_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
                                                   m2m_h + (int64_t)l * 8 * PP, Tp, act_list(t, Tp, l + 1));
   FmmDev<T> dl = d;
   dl.Lc = Mh;
-  if (act_n(t, Tp, L))
-    k_l2p<T><<<act_n(t, Tp, L), 64, sm1, s>>>(dl, t->level_off[L], Tp, mkc<T>(1, 0), act_list(t, Tp, L));
+  HFMM_TRY(launch_l2p<T>(t, dl, Tp, mkc<T>(1, 0), s));
   const double2 cv = make_double2(t->sigma_vol.x, -t->sigma_vol.y);
   const double2 cb = make_double2(t->sigma_bnd.x, -t->sigma_bnd.y);
   HFMM_TRY(p2p_stage<T, 1>(t, d, Sp, Tp, cv, cb, s));
@@ -1873,10 +2248,8 @@ int core_dk_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   C<T>* phd = reinterpret_cast<C<T>*>(t->phis_d);
   const int chunk = 32;
   size_t sm_p2m = (size_t)chunk * P * csz;
-  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
   HFMM_TRY(set_smem<T>((const void*)k_p2m<T, true>, sm_p2m));
-  if (act_n(t, src_set, L))
-    k_p2m<T, false><<<act_n(t, src_set, L), 64, sm_p2m, s>>>(d, d.M, t->level_off[L], src_set, chunk, mkc<T>(1, 0), act_list(t, src_set, L));
+  HFMM_TRY(launch_p2m<T>(t, d, d.M, src_set, mkc<T>(1, 0), s));
   if (act_n(t, src_set, L))
     k_p2m<T, true><<<act_n(t, src_set, L), 64, sm_p2m, s>>>(d, Md, t->level_off[L], src_set, chunk, mkc<T>(1, 0), act_list(t, src_set, L));
   size_t sm8 = 8 * (size_t)P * csz;
@@ -1939,12 +2312,8 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
 
   StageTimer& tm = t->timer;
   // P2M
-  const int chunk = 32;
-  size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
-  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
   tm.begin(HFMM_STAGE_P2M, s);
-  if (act_n(t, src_set, L))
-    k_p2m<T, false><<<act_n(t, src_set, L), 64, sm_p2m, s>>>(d, d.M, t->level_off[L], src_set, chunk, mkc<T>(1, 0), act_list(t, src_set, L));
+  HFMM_TRY(launch_p2m<T>(t, d, d.M, src_set, mkc<T>(1, 0), s));
   tm.end(1, s);
   count_launches(1);
   // M2M, levels L-1 .. 2
@@ -1978,9 +2347,7 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   }
   // L2P then P2P (adds)
   tm.begin(HFMM_STAGE_L2P, s);
-  if (act_n(t, tgt_set, L))
-    k_l2p<T><<<act_n(t, tgt_set, L), 64, sm1, s>>>(d, t->level_off[L], tgt_set, mkc<T>(0, d.k),
-                                                    act_list(t, tgt_set, L));
+  HFMM_TRY(launch_l2p<T>(t, d, tgt_set, mkc<T>(0, d.k), s));
   tm.end(1, s);
   tm.begin(HFMM_STAGE_P2P, s);
   HFMM_TRY(p2p_stage<T, 0>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));
@@ -1991,19 +2358,83 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
 
 }  // namespace
 
-int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol, const double2* q_bnd,
-               double scale_bnd, cudaStream_t s) {
-  unsigned g = ceil_div(t->n_pts, 256);
-  t->timer.begin(HFMM_STAGE_GATHER, s);
+int build_basis_table(fmm_tree* t, cudaStream_t s) {
+  const size_t csz = t->precision == HFMM_FP32 ? sizeof(float2) : sizeof(double2);
+  const size_t bytes = csz * (size_t)t->n_pts * (size_t)t->P;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return HFMM_OK;
+  }
+  if (bytes > fr / 4) return HFMM_OK;  // no table: P2M and L2P evaluate the basis at every apply
+  HFMM_TRY(tree_alloc(t, &t->rtab, bytes));
+  const int nleaf = 1 << (3 * t->L);
   if (t->precision == HFMM_FP32)
-    k_gather<float><<<g, 256, 0, s>>>(t->orig, t->n_pts, t->n_vol, src_set, q_vol, scale_vol, q_bnd,
-                                      scale_bnd, reinterpret_cast<float2*>(t->qs), t->skip);
+    k_basis_table<float><<<nleaf, 64, 0, s>>>(t->xyz, t->leaf_start, t->L, t->p, t->k,
+                                              reinterpret_cast<float2*>(t->rtab));
   else
-    k_gather<double><<<g, 256, 0, s>>>(t->orig, t->n_pts, t->n_vol, src_set, q_vol, scale_vol, q_bnd,
-                                       scale_bnd, reinterpret_cast<double2*>(t->qs), t->skip);
+    k_basis_table<double><<<nleaf, 64, 0, s>>>(t->xyz, t->leaf_start, t->L, t->p, t->k,
+                                               reinterpret_cast<double2*>(t->rtab));
+  return hfmm_last_launch();
+}
+
+namespace {
+
+// original-index range [o0, o1) of a set mask (volume ids, then boundary)
+inline void set_range(const fmm_tree* t, int set, int64_t& o0, int64_t& o1) {
+  o0 = (set & HFMM_SET_VOL) ? 0 : t->n_vol;
+  o1 = (set & HFMM_SET_BND) ? t->n_pts : t->n_vol;
+}
+
+template <typename QB>
+int gather_impl(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol, const QB* q_bnd,
+                double scale_bnd, cudaStream_t s) {
+  int64_t o0, o1;
+  set_range(t, src_set, o0, o1);
+  t->timer.begin(HFMM_STAGE_GATHER, s);
+  if (o1 > o0) {
+    const unsigned g = ceil_div(o1 - o0, 256);
+    if (t->precision == HFMM_FP32)
+      k_gather<float, QB><<<g, 256, 0, s>>>(t->pos_of, o0, o1, t->n_vol, q_vol, scale_vol, q_bnd, scale_bnd,
+                                            reinterpret_cast<float2*>(t->qs), t->skip);
+    else
+      k_gather<double, QB><<<g, 256, 0, s>>>(t->pos_of, o0, o1, t->n_vol, q_vol, scale_vol, q_bnd, scale_bnd,
+                                             reinterpret_cast<double2*>(t->qs), t->skip);
+  }
   t->timer.end(1, s);
   count_launches(1);
   return hfmm_last_launch();
+}
+
+template <typename OB>
+int scatter_impl(fmm_tree* t, const void* sorted, int tgt_set, double2* phi_vol, OB* phi_bnd, cudaStream_t s) {
+  int64_t o0, o1;
+  set_range(t, tgt_set, o0, o1);
+  t->timer.begin(HFMM_STAGE_GATHER, s);
+  if (o1 > o0) {
+    const unsigned g = ceil_div(o1 - o0, 256);
+    if (t->precision == HFMM_FP32)
+      k_scatter<float, OB><<<g, 256, 0, s>>>(t->pos_of, o0, o1, t->n_vol, reinterpret_cast<const float2*>(sorted),
+                                             phi_vol, phi_bnd, t->skip);
+    else
+      k_scatter<double, OB><<<g, 256, 0, s>>>(t->pos_of, o0, o1, t->n_vol,
+                                              reinterpret_cast<const double2*>(sorted), phi_vol, phi_bnd, t->skip);
+  }
+  t->timer.end(1, s);
+  count_launches(1);
+  return hfmm_last_launch();
+}
+
+}  // namespace
+
+int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol, const double2* q_bnd,
+               double scale_bnd, cudaStream_t s) {
+  return gather_impl<double2>(t, src_set, q_vol, scale_vol, q_bnd, scale_bnd, s);
+}
+
+int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol, const float2* q_bnd,
+               double scale_bnd, cudaStream_t s) {
+  return gather_impl<float2>(t, src_set, q_vol, scale_vol, q_bnd, scale_bnd, s);
 }
 
 int fmm_device_error(cudaStream_t s, bool clear) {
@@ -2033,20 +2464,14 @@ int fmm_core_dk(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
 }
 
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cudaStream_t s) {
-  return fmm_scatter_from(t, t->phis, tgt_set, phi_vol, phi_bnd, s);
+  return scatter_impl<double2>(t, t->phis, tgt_set, phi_vol, phi_bnd, s);
+}
+
+int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, float2* phi_bnd, cudaStream_t s) {
+  return scatter_impl<float2>(t, t->phis, tgt_set, phi_vol, phi_bnd, s);
 }
 
 int fmm_scatter_from(fmm_tree* t, const void* sorted, int tgt_set, double2* phi_vol, double2* phi_bnd,
                      cudaStream_t s) {
-  unsigned g = ceil_div(t->n_pts, 256);
-  t->timer.begin(HFMM_STAGE_GATHER, s);
-  if (t->precision == HFMM_FP32)
-    k_scatter<float><<<g, 256, 0, s>>>(t->pos_of, t->n_vol, t->n_bnd, tgt_set,
-                                       reinterpret_cast<const float2*>(sorted), phi_vol, phi_bnd, t->skip);
-  else
-    k_scatter<double><<<g, 256, 0, s>>>(t->pos_of, t->n_vol, t->n_bnd, tgt_set,
-                                        reinterpret_cast<const double2*>(sorted), phi_vol, phi_bnd, t->skip);
-  t->timer.end(1, s);
-  count_launches(1);
-  return hfmm_last_launch();
+  return scatter_impl<double2>(t, sorted, tgt_set, phi_vol, phi_bnd, s);
 }

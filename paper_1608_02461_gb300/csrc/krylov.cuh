@@ -10,17 +10,22 @@
 
 #include "common.cuh"
 
-using DevOp = std::function<int(const double2* in, double2* out)>;
+// operator on complex vectors of real type R (complex128 for double)
+template <typename R>
+using DevOpT = std::function<int(const C<R>* in, C<R>* out)>;
+using DevOp = DevOpT<double>;
 
-struct GmresWork {
+template <typename R>
+struct GmresWorkT {
   int64_t N = 0;
   int m = 0;
   bool flexible = false;
-  double2* V = nullptr;      // (m+1) x N
-  double2* Z = nullptr;      // m x N (flexible)
-  double2* w = nullptr;      // N
-  double2* r = nullptr;      // N
-  double* partial = nullptr; // reduction partials
+  C<R>* V = nullptr;         // (m+1) x N
+  C<R>* Z = nullptr;         // m x N (flexible)
+  C<R>* w = nullptr;         // N
+  C<R>* r = nullptr;         // N
+  double* partial = nullptr; // reduction partials (per block, FP64)
+  unsigned* counter = nullptr; // blocks finished in the current reduction launch (reset by the last)
   double2* dots = nullptr;   // 2 (m+1): CGS2 coefficients
   double2* H = nullptr;      // (m+1) x m, column-major
   double* cs = nullptr;      // m
@@ -33,9 +38,12 @@ struct GmresWork {
   size_t bytes = 0;
   const int* skip = nullptr; // device flag: reductions return at once when set (graph form)
 };
+using GmresWork = GmresWorkT<double>;
 
-int gmres_work_reserve(GmresWork& W, int64_t N, int m, bool flexible);
-void gmres_work_free(GmresWork& W);
+template <typename R>
+int gmres_work_reserve(GmresWorkT<R>& W, int64_t N, int m, bool flexible);
+template <typename R>
+void gmres_work_free(GmresWorkT<R>& W);
 
 struct GmresResult {
   int iters = 0, restarts = 0, converged = 0;
@@ -46,16 +54,19 @@ struct GmresResult {
 // history (host, optional) receives relres_est per iteration.
 // x0_zero: x holds zeros on entry (skips one operator application);
 // true_residual: recompute ||b - A x|| at exit (one more application).
-int gmres_run(GmresWork& W, const DevOp& A, const DevOp* M, const double2* b, double2* x, int m,
+template <typename R>
+int gmres_run(GmresWorkT<R>& W, const DevOpT<R>& A, const DevOpT<R>* M, const C<R>* b, C<R>* x, int m,
               double rtol, int maxit, bool x0_zero, bool true_residual, GmresResult* res,
               double* history, int history_len, cudaStream_t s);
 
-int dev_norm(GmresWork& W, const double2* x, int64_t N, double* out_dev, cudaStream_t s);
+template <typename R>
+int dev_norm(GmresWorkT<R>& W, const C<R>* x, int64_t N, double* out_dev, cudaStream_t s);
 
 // One GMRES cycle of m steps from x0 = 0 for capture in a CUDA graph: no
 // host reads; once the device flag *d_done is set (converged or breakdown)
 // the kernels of the remaining steps return at once (the operator's kernels
 // must honour the same flag).  x = V y with y from the first *d_jdone steps;
 // *d_total += *d_jdone.
-int gmres_cycle_device(GmresWork& W, const DevOp& A, const double2* b, double2* x, int m, double rtol, int* d_done,
-                       int* d_jdone, int* d_total, cudaStream_t s);
+template <typename R>
+int gmres_cycle_device(GmresWorkT<R>& W, const DevOpT<R>& A, const C<R>* b, C<R>* x, int m, double rtol,
+                       int* d_done, int* d_jdone, int* d_total, cudaStream_t s);

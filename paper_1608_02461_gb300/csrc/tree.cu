@@ -463,6 +463,89 @@ __global__ void k_self_terms(double h, double k, double2* out) {
   }
 }
 
+
+// ---------------------------------------------------------------- lattice near-field table
+
+// integer lattice coordinates of each leaf's points: min and max per axis
+// (min > max for an empty leaf)
+__global__ void k_leaf_lat_box(const double* __restrict__ xyz, const int* __restrict__ leaf_start, int nleaf,
+                               double inv_h, int* __restrict__ box) {
+  const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+  if (leaf >= nleaf) return;
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  for (int i = leaf_start[leaf]; i < leaf_start[leaf + 1]; ++i)
+    for (int a = 0; a < 3; ++a) {
+      const int c = (int)llrint(xyz[3 * (int64_t)i + a] * inv_h);
+      lo[a] = min(lo[a], c);
+      hi[a] = max(hi[a], c);
+    }
+  for (int a = 0; a < 3; ++a) {
+    box[6 * leaf + a] = lo[a];
+    box[6 * leaf + 3 + a] = hi[a];
+  }
+}
+
+// largest |offset component| between points of a leaf and of its near leaves
+__global__ void k_lat_max_offset(const int* __restrict__ box, int L, const int* __restrict__ near_off,
+                                 int near_count, int* __restrict__ dmax) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int nleaf = 1 << (3 * L);
+  if (tid >= (int64_t)nleaf * near_count) return;
+  const int leaf = (int)(tid / near_count), q = (int)(tid % near_count);
+  const int* bt = box + 6 * leaf;
+  if (bt[0] > bt[3]) return;
+  const int o = near_off[q];
+  int ix, iy, iz;
+  morton_decode((uint64_t)leaf, ix, iy, iz);
+  const int s = 1 << L;
+  const int jx = ix + (o & 255) - 128, jy = iy + ((o >> 8) & 255) - 128, jz = iz + ((o >> 16) & 255) - 128;
+  if (jx < 0 || jy < 0 || jz < 0 || jx >= s || jy >= s || jz >= s) return;
+  const int* bs = box + 6 * (int)morton_encode(jx, jy, jz);
+  if (bs[0] > bs[3]) return;
+  int m = 0;
+  for (int a = 0; a < 3; ++a) m = max(m, max(bt[3 + a] - bs[a], bs[3 + a] - bt[a]));
+  atomicMax(dmax, m);
+}
+
+__global__ void k_lat_lin(const double* __restrict__ xyz, int64_t n, double inv_h, int W, int* __restrict__ lin) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int cx = (int)llrint(xyz[3 * i] * inv_h), cy = (int)llrint(xyz[3 * i + 1] * inv_h),
+            cz = (int)llrint(xyz[3 * i + 2] * inv_h);
+  lin[i] = (cz * W + cy) * W + cx;
+}
+
+// half table over delta = (dz W + dy) W + dx >= 0 (dx, dy, dz in [-D, D]):
+// G(h d) = e^{i k h |d|} / (4 pi h |d|) (the 3D Green's function of Sec. 5.2 on the lattice), zero at d = 0
+__global__ void k_lat_table(int D, double h, double k, int64_t nhalf, int64_t npad, double2* __restrict__ t64,
+                            float2* __restrict__ t32) {
+  const int W = 2 * D + 1;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= npad) return;
+  double2 g = make_double2(0.0, 0.0);
+  if (e < nhalf) {
+    // balanced base-W digits of e
+    int64_t r = e;
+    int dx = (int)(((r % W) + W) % W);
+    if (dx > D) dx -= W;
+    r = (r - dx) / W;
+    int dy = (int)(((r % W) + W) % W);
+    if (dy > D) dy -= W;
+    r = (r - dy) / W;
+    const int dz = (int)r;
+    const int d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 > 0) {
+      const double rr = h * sqrt((double)d2);
+      double sn, cs;
+      sincos(k * rr, &sn, &cs);
+      const double a = 0.07957747154594766788 / rr;
+      g = make_double2(a * cs, a * sn);
+    }
+  }
+  t64[e] = g;
+  t32[e] = make_float2((float)g.x, (float)g.y);
+}
+
 }  // namespace
 
 int build_geometry_and_sort(fmm_tree* t, const double* d_vol, const double* d_bnd, cudaStream_t s) {
@@ -717,5 +800,41 @@ int build_active_lists(fmm_tree* t, cudaStream_t s) {
     t->act_cells[m] = cells + m * t->total_cells;
     for (int l = 0; l <= HFMM_MAX_LEVEL; ++l) t->act_count[m][l] = h[m * (HFMM_MAX_LEVEL + 1) + l];
   }
+  return HFMM_OK;
+}
+
+int build_lattice_table(fmm_tree* t, cudaStream_t s) {
+  t->lat_D = 0;
+  if (!t->lattice || t->near_count == 0) return HFMM_OK;
+  const int nleaf = 1 << (3 * t->L);
+  const double inv_h = 1.0 / t->h;
+  int *box = nullptr, *dmax = nullptr;
+  HFMM_CUDA_TRY(cudaMallocAsync((void**)&box, sizeof(int) * 6 * nleaf + sizeof(int) * 64, s));
+  dmax = box + 6 * nleaf;
+  HFMM_CUDA_TRY(cudaMemsetAsync(dmax, 0, sizeof(int), s));
+  k_leaf_lat_box<<<ceil_div(nleaf, 128), 128, 0, s>>>(t->xyz, t->leaf_start, nleaf, inv_h, box);
+  k_lat_max_offset<<<ceil_div((int64_t)nleaf * t->near_count, 256), 256, 0, s>>>(box, t->L, t->near_off,
+                                                                                 t->near_count, dmax);
+  HFMM_TRY(hfmm_last_launch());
+  int D = 0;
+  HFMM_CUDA_TRY(cudaMemcpyAsync(&D, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaFreeAsync(box, s);
+  const int W = 2 * D + 1;
+  const int64_t nhalf = ((int64_t)W * W * W + 1) / 2;
+  const int64_t npad = (nhalf + 1) / 2 * 2;  // multiple of 16 bytes in both precisions
+  // the table is staged whole in shared memory by the near-field kernel
+  if (D < 1 || npad * (int64_t)sizeof(float2) > HFMM_LAT_TABLE_MAX_BYTES) return HFMM_OK;
+  HFMM_TRY(tree_alloc_t(t, &t->lat_lin, t->n_pts));
+  HFMM_TRY(tree_alloc_t(t, &t->lat_tab32, npad));
+  HFMM_TRY(tree_alloc_t(t, &t->lat_tab64, npad));
+  k_lat_lin<<<ceil_div(t->n_pts, 256), 256, 0, s>>>(t->xyz, t->n_pts, inv_h, W, t->lat_lin);
+  k_lat_table<<<ceil_div(npad, 256), 256, 0, s>>>(D, t->h, t->k, nhalf, npad, t->lat_tab64, t->lat_tab32);
+  HFMM_TRY(hfmm_last_launch());
+  t->lat_half = npad;
+  // FP64: table, window of 32-byte staged sources and 4 KB of static shared memory
+  t->lat_tab64_fits = npad * (int64_t)sizeof(double2) + (int64_t)HFMM_LAT_WS * 32 + 4096 <= HFMM_SMEM_MAX;
+  t->lat_D = D;
+  t->lat_W = W;
   return HFMM_OK;
 }

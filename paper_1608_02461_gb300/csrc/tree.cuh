@@ -192,6 +192,27 @@ struct fmm_tree {
   int tuned_variant[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
   int tuned_fill[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 
+  // ---- near-field kernel table of lattice trees: every point is a node of
+  //      the lattice h Z^3, so the kernel between two points depends only on
+  //      their integer offset d in [-D, D]^3 (D: largest offset component
+  //      between points of near leaves), coded as delta = lin_t - lin_s with
+  //      lin = (iz W + iy) W + ix, W = 2D + 1; G(d) = G(-d), so a half table
+  //      lat_tab[|delta|] = e^{ik h|d|} / (4 pi h|d|) (0 at d = 0) holds all
+  int lat_D = 0;                // 0: no table
+  int lat_W = 0;                // 2 lat_D + 1
+  int64_t lat_half = 0;         // (W^3 + 1) / 2 entries, padded to a multiple of 16 bytes (FP64 size)
+  int* lat_lin = nullptr;       // [n_pts] lin of each sorted point
+  float2* lat_tab32 = nullptr;  // [lat_half] FP32 table
+  double2* lat_tab64 = nullptr; // [lat_half] FP64 table
+  int lat_tab64_fits = 0;       // the FP64 table fits the near-field kernel's shared memory
+  int use_lattice_p2p = 1;      // near field through the table when it exists
+
+  // ---- regular basis table [n_pts][P]: R_a(x_i - c) for each sorted point
+  //      and its leaf centre (precision of the form); P2M and L2P read it
+  //      instead of evaluating Bessel and Legendre functions per apply
+  void* rtab = nullptr;
+  int use_rtab = 1;
+
   // ---- operators (FP64 master copy; FP32 copy for the FP32 form)
   double2* op_m2m = nullptr;    // [L+1][8][P][P]   row a' (out), column a (in)
   double2* op_l2l = nullptr;    // [L+1][8][P][P]
@@ -235,6 +256,8 @@ struct fmm_tree {
   // ---- preconditioner work (complex128)
   double2* g_bnd = nullptr;     // [n_bnd]
   double2* q_bnd = nullptr;     // [n_bnd]
+  float2* g_bnd32 = nullptr;    // [n_bnd] the same for the complex64 inner solve of the FP32 form
+  float2* q_bnd32 = nullptr;
 
   // ---- counters
   int64_t m2l_pairs = 0, p2p_pairs = 0;
@@ -264,6 +287,9 @@ int build_self_terms(fmm_tree* t, cudaStream_t s);
 int build_pair_counts(fmm_tree* t, cudaStream_t s);
 int build_m2l_tiles(fmm_tree* t, cudaStream_t s);
 int build_active_lists(fmm_tree* t, cudaStream_t s);
+int build_lattice_table(fmm_tree* t, cudaStream_t s);
+// fmm.cu: regular basis table (skipped when it would take over a quarter of free memory)
+int build_basis_table(fmm_tree* t, cudaStream_t s);
 double p2p_work(const fmm_tree* t, int src_set, int tgt_set);
 double m2l_work(const fmm_tree* t, int src_set, int tgt_set);
 
@@ -275,6 +301,9 @@ int build_operators_adjoint(fmm_tree* t, cudaStream_t s);
 // fmm.cu: sorted-weight gather, FMM core over the sorted vectors, scatter
 int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol,
                const double2* q_bnd, double scale_bnd, cudaStream_t s);
+// the same with a complex64 boundary vector
+int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol,
+               const float2* q_bnd, double scale_bnd, cudaStream_t s);
 int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
 // adjoint pass: weights in qs on the points of tgt_set, result in phis on src_set
 int fmm_core_adjoint(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
@@ -283,6 +312,7 @@ int fmm_core_dk(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
 // HFMM_ERR_TIMEOUT (or 0) recorded by a kernel's bounded wait; synchronises s
 int fmm_device_error(cudaStream_t s, bool clear);
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cudaStream_t s);
+int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, float2* phi_bnd, cudaStream_t s);
 int fmm_scatter_from(fmm_tree* t, const void* sorted, int tgt_set, double2* phi_vol, double2* phi_bnd,
                      cudaStream_t s);
 

@@ -213,3 +213,44 @@ def test_graph_preconditioner_equals_host_driven(prec):
         # a second solve replays the captured graph
         xg2, ig2 = tg.gmres(b, **kw)
         assert torch.equal(xg2, xh) and ig2.iters == ih.iters
+
+
+def _tree_with_env(env, *args):
+    """A tree built while the given environment switches are set (they are
+    read when the handle is built)."""
+    import os
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        return hfmm.Tree(*args)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", [(16, 9.0, 6, 32, 0.4), (13, 25.0, 4, 16, 0.35)])
+def test_lattice_tables_match_generic_paths(prec, case):
+    """Lattice trees evaluate the near field through the kernel table over
+    integer offsets and P2M/L2P through the per-point regular-basis table;
+    both give the results of the per-pair / per-point evaluation (rounding
+    only), for every pass, in both precisions, and in adjoint mode."""
+    n, k, p, leaf, th = case
+    fast = hfmm.Tree(n, k, p, th, leaf, prec)
+    slow = _tree_with_env({"HFMM_LATTICE_P2P": "0", "HFMM_BASIS_TABLE": "0"}, n, k, p, th, leaf, prec)
+    qv = inputs.complex_normal(n ** 3, 5)
+    qb = inputs.complex_normal(6 * n * n, 6)
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    for src, tgt in [(3, 3), (1, 2), (2, 2), (3, 1)]:
+        a = run_apply(fast, qv if src & 1 else None, qb if src & 2 else None, src, tgt)
+        b = run_apply(slow, qv if src & 1 else None, qb if src & 2 else None, src, tgt)
+        assert rel(a, b) < tol, (src, tgt, rel(a, b))
+    tv, tb = torch.from_numpy(qv).to(DEV), torch.from_numpy(qb).to(DEV)
+    fa = fast.apply(tv, tb, src=3, tgt=3, mode=hfmm.ADJ)
+    sa = slow.apply(tv, tb, src=3, tgt=3, mode=hfmm.ADJ)
+    torch.cuda.synchronize()
+    for x, y in zip(fa, sa):
+        assert (torch.linalg.vector_norm(x - y) / torch.linalg.vector_norm(y)).item() < tol
