@@ -80,6 +80,11 @@ void release(fmm_tree* t) {
   t->bufs.clear();
   if (t->ev0) cudaEventDestroy(t->ev0);
   if (t->ev1) cudaEventDestroy(t->ev1);
+  if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+  if (t->ev_join) cudaEventDestroy(t->ev_join);
+  if (t->near_stream) cudaStreamDestroy(t->near_stream);
+  t->ev_fork = t->ev_join = nullptr;
+  t->near_stream = nullptr;
   t->timer.destroy();
   if (t->gaunt) cudaFree(t->gaunt);
   t->gaunt = nullptr;
@@ -158,6 +163,7 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   if (const char* v = getenv("HFMM_M2L_VARIANT")) t->m2l_variant = atoi(v);
   if (const char* v = getenv("HFMM_LATTICE_P2P")) t->use_lattice_p2p = atoi(v) != 0;
   if (const char* v = getenv("HFMM_BASIS_TABLE")) t->use_rtab = atoi(v) != 0;
+  if (const char* v = getenv("HFMM_OVERLAP_NEAR")) t->overlap_near = atoi(v) != 0;
   HFMM_TRY(tree_alloc(t, &t->m2l_part, csz * t->total_cells * P * t->m2l_part_max));
   HFMM_TRY(tree_alloc_t(t, &t->g_bnd, t->n_bnd + 1));
   HFMM_TRY(tree_alloc_t(t, &t->q_bnd, t->n_bnd + 1));
@@ -178,6 +184,10 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   HFMM_TRY(build_basis_table(t, s));
   HFMM_CUDA_TRY(cudaEventCreate(&t->ev0));
   HFMM_CUDA_TRY(cudaEventCreate(&t->ev1));
+  HFMM_TRY(tree_alloc(t, &t->phis_near, csz * N));
+  HFMM_CUDA_TRY(cudaStreamCreateWithFlags(&t->near_stream, cudaStreamNonBlocking));
+  HFMM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming));
+  HFMM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming));
   HFMM_CUDA_TRY(cudaStreamSynchronize(s));
   return HFMM_OK;
 }

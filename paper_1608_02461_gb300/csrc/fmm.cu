@@ -41,7 +41,23 @@ struct FmmDev {
   int p, P, L;
   T k;
   const int* skip;  // when set and nonzero, every kernel of the pass returns at once
+  C<T>* near;       // when set: P2P writes its sums here (=) and L2P adds them
 };
+
+// P2P result of target i: into the near-field buffer, or added to phis
+template <typename T>
+__device__ __forceinline__ void p2p_store(const FmmDev<T>& d, int i, C<T> v) {
+  if (d.near)
+    d.near[i] = v;
+  else
+    d.phis[i] = cadd<T>(d.phis[i], v);
+}
+
+// L2P result of target i (plus the near field when it went to its own buffer)
+template <typename T>
+__device__ __forceinline__ void l2p_store(const FmmDev<T>& d, int i, C<T> v) {
+  d.phis[i] = d.near ? cadd<T>(v, d.near[i]) : v;
+}
 
 #define HFMM_SKIP_IF(d) \
   if ((d).skip && *(d).skip) return
@@ -288,7 +304,7 @@ __global__ void __launch_bounds__(256) k_l2p_tab(FmmDev<T> d, const C<T>* __rest
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
     }
-    if (act && sub == 0) d.phis[i] = cmul<T>(fac, acc);
+    if (act && sub == 0) l2p_store<T>(d, i, cmul<T>(fac, acc));
   }
 }
 
@@ -1401,7 +1417,7 @@ __global__ void k_l2p(FmmDev<T> d, int64_t leaf_off, int tgt_set, C<T> fac, cons
       er = nr;
       ei = ni;
     }
-    d.phis[i] = cmul<T>(fac, acc);
+    l2p_store<T>(d, i, cmul<T>(fac, acc));
   }
 }
 
@@ -1565,7 +1581,7 @@ __global__ void k_p2p(FmmDev<T> d, const int* near_off, int near_count, int src_
         double2 sg = is_vol ? sig_vol : sig_bnd;
         cfma<T>(tot, mkc<T>(T(sg.x), T(sg.y)), d.qs[i]);
       }
-      d.phis[i] = cadd<T>(d.phis[i], tot);
+      p2p_store<T>(d, i, tot);
     }
   }
 }
@@ -1758,7 +1774,7 @@ __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restri
         double2 sg = is_vol ? sig_vol : sig_bnd;
         cfma<T>(tot, mkc<T>(T(sg.x), T(sg.y)), d.qs[i]);
       }
-      d.phis[i] = cadd<T>(d.phis[i], tot);
+      p2p_store<T>(d, i, tot);
     }
   }
 }
@@ -1952,7 +1968,7 @@ __global__ void __launch_bounds__(LAT_THREADS, sizeof(T) == 4 ? 2 : 1)
           const double2 sg = is_vol ? sig_vol : sig_bnd;  // conjugated by the caller in adjoint mode
           cfma<T>(tot, mkc<T>(T(sg.x), T(sg.y)), d.qs[i]);
         }
-        d.phis[i] = cadd<T>(d.phis[i], tot);
+        p2p_store<T>(d, i, tot);
       }
     }
   }
@@ -2012,6 +2028,7 @@ FmmDev<T> make_dev(fmm_tree* t) {
   d.L = t->L;
   d.k = T(t->k);
   d.skip = t->skip;
+  d.near = nullptr;
   return d;
 }
 
@@ -2311,6 +2328,21 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   (void)nleaf;
 
   StageTimer& tm = t->timer;
+  // near field on its own stream, concurrent with the far-field chain, when
+  // the targets are the boundary points: there the far-field kernels are
+  // small and latency-bound and leave most SMs idle (with volume targets both
+  // chains are compute-bound and running them together is slower)
+  const bool overlap = t->overlap_near && t->near_stream && t->phis_near && !(tgt_set & HFMM_SET_VOL);
+  if (overlap) {
+    d.near = reinterpret_cast<C<T>*>(t->phis_near);
+    cudaStream_t sn = t->near_stream;
+    HFMM_CUDA_TRY(cudaEventRecord(t->ev_fork, s));
+    HFMM_CUDA_TRY(cudaStreamWaitEvent(sn, t->ev_fork, 0));
+    tm.begin(HFMM_STAGE_P2P, sn);
+    HFMM_TRY(p2p_stage<T, 0>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, sn));
+    tm.end(1, sn, tm.on ? p2p_work(t, src_set, tgt_set) : 0.0);
+    HFMM_CUDA_TRY(cudaEventRecord(t->ev_join, sn));
+  }
   // P2M
   tm.begin(HFMM_STAGE_P2M, s);
   HFMM_TRY(launch_p2m<T>(t, d, d.M, src_set, mkc<T>(1, 0), s));
@@ -2345,13 +2377,16 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
     tm.end(L - 2, s);
     count_launches(L - 2);
   }
-  // L2P then P2P (adds)
+  // L2P (adds the near field when it ran concurrently), else L2P then P2P (adds)
+  if (overlap) HFMM_CUDA_TRY(cudaStreamWaitEvent(s, t->ev_join, 0));
   tm.begin(HFMM_STAGE_L2P, s);
   HFMM_TRY(launch_l2p<T>(t, d, tgt_set, mkc<T>(0, d.k), s));
   tm.end(1, s);
-  tm.begin(HFMM_STAGE_P2P, s);
-  HFMM_TRY(p2p_stage<T, 0>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));
-  tm.end(1, s, tm.on ? p2p_work(t, src_set, tgt_set) : 0.0);
+  if (!overlap) {
+    tm.begin(HFMM_STAGE_P2P, s);
+    HFMM_TRY(p2p_stage<T, 0>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));
+    tm.end(1, s, tm.on ? p2p_work(t, src_set, tgt_set) : 0.0);
+  }
   count_launches(2);
   return hfmm_last_launch();
 }

@@ -213,6 +213,14 @@ struct fmm_tree {
   void* rtab = nullptr;
   int use_rtab = 1;
 
+  // ---- near field concurrent with the far field: P2P runs on its own
+  //      stream (fork/join through events, also inside captured graphs) into
+  //      phis_near, and L2P adds it
+  cudaStream_t near_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  void* phis_near = nullptr;    // [n_pts] precision T
+  int overlap_near = 1;
+
   // ---- operators (FP64 master copy; FP32 copy for the FP32 form)
   double2* op_m2m = nullptr;    // [L+1][8][P][P]   row a' (out), column a (in)
   double2* op_l2l = nullptr;    // [L+1][8][P][P]
