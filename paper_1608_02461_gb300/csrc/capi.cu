@@ -86,6 +86,7 @@ void release(fmm_tree* t) {
   t->ev_fork = t->ev_join = nullptr;
   t->near_stream = nullptr;
   t->timer.destroy();
+  m2l_tc_release(t);
   if (t->gaunt) cudaFree(t->gaunt);
   t->gaunt = nullptr;
 }
@@ -164,6 +165,7 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   if (const char* v = getenv("HFMM_LATTICE_P2P")) t->use_lattice_p2p = atoi(v) != 0;
   if (const char* v = getenv("HFMM_BASIS_TABLE")) t->use_rtab = atoi(v) != 0;
   if (const char* v = getenv("HFMM_OVERLAP_NEAR")) t->overlap_near = atoi(v) != 0;
+  if (const char* v = getenv("HFMM_M2L_TC")) t->use_m2l_tcore = atoi(v);
   HFMM_TRY(tree_alloc(t, &t->m2l_part, csz * t->total_cells * P * t->m2l_part_max));
   HFMM_TRY(tree_alloc_t(t, &t->g_bnd, t->n_bnd + 1));
   HFMM_TRY(tree_alloc_t(t, &t->q_bnd, t->n_bnd + 1));

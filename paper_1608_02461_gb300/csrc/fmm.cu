@@ -1299,10 +1299,10 @@ int launch_m2l_pairs(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_s
 
 template <typename T, int CM, int R, int RT>
 int launch_m2l_tma_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
-                      int accumulate, cudaStream_t s) {
+                      int accumulate, cudaStream_t s, int nt_limit) {
   const int P = t->P, mi = tgt_set - 1;
   const int TC = 8 * CM;
-  const int nt = t->m2l_ntiles[mi];
+  const int nt = nt_limit >= 0 ? std::min(nt_limit, t->m2l_ntiles[mi]) : t->m2l_ntiles[mi];
   if (nt == 0) return HFMM_OK;
   HFMM_TRY(m2l_valid_lists(t, src_set, tgt_set, s));
   const int ci = mi * 3 + (src_set - 1);
@@ -1340,14 +1340,14 @@ int launch_m2l_tma_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_
 
 template <typename T, int CM>
 int launch_m2l_tma(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_set, int tgt_set,
-                   int accumulate, cudaStream_t s) {
+                   int accumulate, cudaStream_t s, int nt_limit = -1) {
   const int P = t->P;
-  if (P <= 16) return launch_m2l_tma_rt<T, CM, 1, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
-  if (P <= 32) return launch_m2l_tma_rt<T, CM, 2, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
-  if (P <= 36) return launch_m2l_tma_rt<T, CM, 3, 12>(t, d, ops, src_set, tgt_set, accumulate, s);
-  if (P <= 48) return launch_m2l_tma_rt<T, CM, 3, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
-  if (P <= 64) return launch_m2l_tma_rt<T, CM, 4, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
-  if (P <= 96) return launch_m2l_tma_rt<T, CM, 6, 16>(t, d, ops, src_set, tgt_set, accumulate, s);
+  if (P <= 16) return launch_m2l_tma_rt<T, CM, 1, 16>(t, d, ops, src_set, tgt_set, accumulate, s, nt_limit);
+  if (P <= 32) return launch_m2l_tma_rt<T, CM, 2, 16>(t, d, ops, src_set, tgt_set, accumulate, s, nt_limit);
+  if (P <= 36) return launch_m2l_tma_rt<T, CM, 3, 12>(t, d, ops, src_set, tgt_set, accumulate, s, nt_limit);
+  if (P <= 48) return launch_m2l_tma_rt<T, CM, 3, 16>(t, d, ops, src_set, tgt_set, accumulate, s, nt_limit);
+  if (P <= 64) return launch_m2l_tma_rt<T, CM, 4, 16>(t, d, ops, src_set, tgt_set, accumulate, s, nt_limit);
+  if (P <= 96) return launch_m2l_tma_rt<T, CM, 6, 16>(t, d, ops, src_set, tgt_set, accumulate, s, nt_limit);
   return HFMM_ERR_UNSUPPORTED;
 }
 
@@ -2073,6 +2073,24 @@ int m2l_stage(fmm_tree* t, const FmmDev<T>& d, const C<T>* m2l, int src_set, int
                                                  : (t->m2l_pairs_enabled && tgt_set == HFMM_SET_BND &&
                                                     src_set == HFMM_SET_BND);
     if (pairs) return launch_m2l_pairs<T>(t, d, m2l, src_set, tgt_set, accumulate, s);
+    // tensor cores for the levels >= lmin of the forward far field (volume
+    // targets by default), the tiled kernel for the levels below
+    if constexpr (sizeof(T) == 4) {
+      const int lmin = m2l_tc_lmin(t);
+      const bool fwd = (const void*)m2l == (const void*)t->op_m2l32 && (void*)d.M == t->M && (void*)d.Lc == t->Lc;
+      const bool pass_ok = t->use_m2l_tcore >= 2 || (tgt_set & HFMM_SET_VOL);
+      if (lmin && fwd && pass_ok) {
+        const int nlow = t->m2l_tiles_lt[tgt_set - 1][lmin];
+        if (nlow > 0) {
+          if (t->m2l_tc == 32) HFMM_TRY(launch_m2l_tma<T, 4>(t, d, m2l, src_set, tgt_set, accumulate, s, nlow));
+          else HFMM_TRY(launch_m2l_tma<T, 2>(t, d, m2l, src_set, tgt_set, accumulate, s, nlow));
+        }
+        int ntc = 0;
+        HFMM_TRY(m2l_tc_stage(t, src_set, tgt_set, accumulate, s, &ntc));
+        count_launches(ntc);
+        return HFMM_OK;
+      }
+    }
     if (t->m2l_tc == 32) return launch_m2l_tma<T, 4>(t, d, m2l, src_set, tgt_set, accumulate, s);
     return launch_m2l_tma<T, 2>(t, d, m2l, src_set, tgt_set, accumulate, s);
   }
@@ -2480,8 +2498,11 @@ int fmm_device_error(cudaStream_t s, bool clear) {
     int z = 0;
     HFMM_CUDA_TRY(cudaMemcpyToSymbolAsync(g_fmm_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
   }
+  if (m2l_tc_error(s, clear)) h = HFMM_ERR_TIMEOUT;
   return h;
 }
+
+int set_smem_any(const void* fn, size_t bytes) { return set_smem<float>(fn, bytes); }
 
 int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   if (t->precision == HFMM_FP32) return core_impl<float>(t, src_set, tgt_set, s);

@@ -1,0 +1,619 @@
+// M2L on the tensor cores (FP32 form, dense far-field passes).
+//
+// At a level l >= lmin the multipole expansions are re-laid out per parity
+// class of the cells (x, y, z bits 0) as dense lattices X[c][z][y][x][2P]
+// (complex interleaved, 2P floats a row; cells without sources of the pass
+// hold zeros).  Every cell of a class shares one M2L offset list (Sec. 5.1.2
+// interaction lists), and for an offset o the sources of a brick of 8 x 4 x 4
+// same-class target cells form a brick of one class at a shifted origin.  So
+// one CTA owns such a brick (128 target cells) and, for each offset of its
+// list, accumulates the real form of the complex product
+//     D[cell][2a'+c'] += sum_k X_src[cell][k] B_o[k][2a'+c'],
+//     B_o[2a][2a'] = B_o[2a+1][2a'+1] = Re T_o(a', a),
+//     B_o[2a][2a'+1] = Im T_o(a', a) = -B_o[2a+1][2a'],
+// with tcgen05.mma (kind::tf32, M = 128 cells, N = 2P rounded up to 16,
+// K = 8 per instruction) into a TMEM accumulator.  The source brick arrives
+// by one 5-D TMA load per 32-float slice of K (zero fill outside the level);
+// the operator slice by a 1-D bulk copy of a pre-swizzled image.  Both use
+// the 128-byte swizzled K-major layout (8-row atoms of 1024 bytes).
+//
+// FP32 accuracy from TF32 inputs: every operand is split as v = hi + lo with
+// hi = v truncated to TF32 (exact in TF32) and lo = v - hi, and the product is
+// hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).
+//
+// Warp roles (192 threads): warp 4 lane 0 issues the copies of a ring of
+// NSTG stages; warp 5 lane 0 issues the MMAs, commits each stage back to the
+// producer, and accumulates chunks of CHUNK offsets alternately into two
+// TMEM buffers; warps 0-3 (TMEM lanes 32w..32w+31 = brick cells) add each
+// finished chunk to FP32 registers and free its buffer, then write the
+// result.  Tensor-core accumulation rounds less carefully than FP32 FMA, so
+// bounding its chains to one chunk keeps the FP32 form's accuracy.  Every
+// wait is bounded (about one second); on time-out the kernel records
+// HFMM_ERR_TIMEOUT, waits (bounded) for its own copies and MMAs in flight,
+// frees its TMEM and returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <new>
+
+#include "tree.cuh"
+
+namespace {
+
+constexpr int TC_ACC_WARPS = 4;                      // warps that read TMEM lanes 0..127
+constexpr int TC_THREADS = 32 * (TC_ACC_WARPS + 2);  // + producer warp + MMA warp
+constexpr int TC_NSTG = 3;
+constexpr int TC_CHUNK = 8;       // offsets per tensor-core accumulation chain
+constexpr int TC_MAX_NPAD = 128;  // accumulator columns (2P rounded up to 16)
+constexpr int TC_TMEM_COLS = 256; // two accumulator buffers of 128 columns
+constexpr int BX = 8, BY = 4, BZ = 4;  // brick of same-class target cells (128 rows)
+constexpr int TC_MAX_COUNT = 2048;     // offsets per class list held in shared memory
+
+__device__ int g_tc_error;  // set when a bounded wait gives up
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tc_mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void tc_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool tc_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(sa(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t tc_now() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: false after about one second
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+  if (tc_try_wait(bar, parity)) return true;
+  const uint64_t t0 = tc_now();
+  while (tc_now() - t0 < 1000000000ull)
+    if (tc_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tc_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sa(dst)),
+      "l"(src), "r"(bytes), "r"(sa(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_tma5(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                        uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(sa(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(sa(bar))
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset); the start address advances by 32 bytes
+// per K step of 8 TF32 inside an atom
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: D F32, A and B TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive accumulator columns of this thread's TMEM lane (whole warp)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__host__ __device__ __forceinline__ float tf32_hi(float v) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+#else
+  return v;
+#endif
+}
+
+// X_hi / X_lo of level l: per class c and half coordinates, 2P floats a row;
+// zero for cells holding no source of src_set
+__global__ void k_tc_split(const float* __restrict__ M, const int* __restrict__ flags, int64_t off, int l, int twoP,
+                           int src_set, float* __restrict__ xh, float* __restrict__ xl, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t ncell = (int64_t)1 << (3 * l);
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ncell * twoP) return;
+  const int64_t m = e / twoP;
+  const int k = (int)(e - m * twoP);
+  int ix, iy, iz;
+  morton_decode((uint64_t)m, ix, iy, iz);
+  const int h = 1 << (l - 1);
+  const int c = (ix & 1) | ((iy & 1) << 1) | ((iz & 1) << 2);
+  const int64_t row = (((int64_t)c * h + (iz >> 1)) * h + (iy >> 1)) * h + (ix >> 1);
+  const float v = (flags[off + m] & src_set) ? M[(off + m) * twoP + k] : 0.f;
+  const float hv = tf32_hi(v);
+  xh[row * twoP + k] = hv;
+  xl[row * twoP + k] = v - hv;
+}
+
+// Pre-swizzled operator images: for each (level, slot), NA slices of
+// [Npad rows n][32 floats k] in the 128-byte swizzled K-major layout, hi
+// slices then lo slices; B^T[n][k] as in the header comment, zero outside
+// n, k < 2P.  One-time, at the first tensor-core M2L of a tree.
+__global__ void k_tc_ops(const float2* __restrict__ ops, int P, int64_t box_cells, int lmin, int L, int NA, int Npad,
+                         float* __restrict__ img) {
+  const int64_t per_slot = (int64_t)2 * NA * Npad * 32;  // floats
+  const int64_t nslot = (int64_t)(L - lmin + 1) * box_cells;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nslot * NA * Npad * 32) return;
+  const int64_t sl = e / ((int64_t)NA * Npad * 32);
+  int64_t r = e - sl * ((int64_t)NA * Npad * 32);
+  const int a = (int)(r / (Npad * 32));
+  r -= (int64_t)a * Npad * 32;
+  const int n = (int)(r / 32), kk = (int)(r % 32);
+  const int k = 32 * a + kk;
+  const int level = lmin + (int)(sl / box_cells);
+  const int64_t slot = sl % box_cells;
+  float v = 0.f;
+  if (n < 2 * P && k < 2 * P) {
+    const int ap = n >> 1, cp = n & 1, ai = k >> 1, ci = k & 1;
+    const float2 T = ops[((int64_t)level * box_cells + slot) * P * P + (int64_t)ap * P + ai];
+    // B^T[2a'+c'][2a+c]: (c',c) = (0,0) Re T, (0,1) -Im T, (1,0) Im T, (1,1) Re T
+    v = (cp == ci) ? T.x : (cp == 0 ? -T.y : T.y);
+  }
+  const float hv = tf32_hi(v);
+  // swizzled position of (n, kk) in the slice: 16-byte chunk (kk / 4) ^ (n % 8)
+  const int64_t pos = (int64_t)n * 32 + (((kk >> 2) ^ (n & 7)) << 2) + (kk & 3);
+  float* base = img + sl * per_slot + (int64_t)a * Npad * 32;
+  base[pos] = hv;
+  base[(int64_t)NA * Npad * 32 + pos] = v - hv;
+}
+
+struct TcMaps {
+  CUtensorMap xh[HFMM_MAX_LEVEL + 1];
+  CUtensorMap xl[HFMM_MAX_LEVEL + 1];
+};
+
+struct TcArgs {
+  const float* img;         // operator images
+  const int* m2l_off;       // [8][count] packed offsets
+  const int* m2l_slot;      // [8][count] operator slot of each offset
+  const int* flags;         // all levels
+  const int64_t* level_off; // device copy
+  float* Lc;                // local expansions (complex interleaved)
+  float* part;              // split partial sums [nsplit][total_cells][2P], or null
+  const int* skip;          // every kernel of the pass returns at once when set
+  int64_t part_stride;      // floats
+  int count;                // offsets per class
+  int64_t box_cells;
+  int P, NA, Npad, lmin, L;
+  int tgt_set, accumulate;
+  int brick_first[HFMM_MAX_LEVEL + 2];  // first CTA of each level
+};
+
+__device__ __forceinline__ void tc_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant__ TcMaps maps, const TcArgs A) {
+  if (A.skip && *A.skip) return;
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  // 1024-byte aligned stage buffers (the launch adds 1024 bytes of slack)
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full[TC_NSTG], empty[TC_NSTG], ready[2], drained[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int vlist[TC_MAX_COUNT];
+  __shared__ unsigned char vflag[TC_MAX_COUNT];
+  __shared__ int nvalid;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int twoP = 2 * A.P;
+  const uint32_t xbytes = (uint32_t)(BX * BY * BZ * 128);  // one K slice of a brick
+  const uint32_t bbytes = (uint32_t)A.Npad * 128;          // one K slice of an operator
+  const uint32_t stage_bytes = 2 * xbytes + 2 * bbytes;
+
+  // this CTA's brick: level, class, origin in half coordinates
+  int level = A.lmin;
+  while (level < A.L && (int)blockIdx.x >= A.brick_first[level + 1]) ++level;
+  const int h = 1 << (level - 1);
+  const int nbx = h / BX, nby = h / BY, nbz = h / BZ;
+  int b = (int)blockIdx.x - A.brick_first[level];
+  const int cls = b / (nbx * nby * nbz);
+  b -= cls * nbx * nby * nbz;
+  const int hz0 = (b / (nbx * nby)) * BZ;
+  b %= nbx * nby;
+  const int hy0 = (b / nbx) * BY, hx0 = (b % nbx) * BX;
+  const int cx = cls & 1, cy = (cls >> 1) & 1, cz = (cls >> 2) & 1;
+
+  if (tid == 0) {
+    for (int s = 0; s < TC_NSTG; ++s) {
+      tc_mbar_init(&full[s], 1);
+      tc_mbar_init(&empty[s], 1);
+    }
+    for (int j = 0; j < 2; ++j) {
+      tc_mbar_init(&ready[j], 1);
+      tc_mbar_init(&drained[j], TC_ACC_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&tmem_base)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // offsets of this CTA's share of the class list whose source brick meets
+  // the level, in list order
+  const int ks = blockIdx.y, kn = gridDim.y;
+  const int i0 = (int)((int64_t)A.count * ks / kn), i1 = (int)((int64_t)A.count * (ks + 1) / kn);
+  for (int i = i0 + tid; i < i1; i += TC_THREADS) {
+    const int o = A.m2l_off[cls * A.count + i];
+    const int ox = (o & 255) - 128, oy = ((o >> 8) & 255) - 128, oz = ((o >> 16) & 255) - 128;
+    const int sx = hx0 + ((cx + ox) >> 1), sy = hy0 + ((cy + oy) >> 1), sz = hz0 + ((cz + oz) >> 1);
+    vflag[i - i0] = (sx + BX > 0 && sx < h && sy + BY > 0 && sy < h && sz + BZ > 0 && sz < h) ? 1 : 0;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int base = 0;
+    for (int c0 = 0; c0 < i1 - i0; c0 += 32) {
+      const int j = c0 + lane;
+      const bool f = j < i1 - i0 && vflag[j];
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (f) vlist[base + __popc(bal & ((1u << lane) - 1u))] = i0 + j;
+      base += __popc(bal);
+    }
+    if (lane == 0) nvalid = base;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const int NA = A.NA;
+  const int nv = nvalid;
+  const int units = nv * NA;
+  const int cunits = TC_CHUNK * NA;                      // units per accumulation chunk
+  const int nchunks = (nv + TC_CHUNK - 1) / TC_CHUNK;
+  const uint32_t idesc = tc_idesc(128, A.Npad);
+
+  if (warp == TC_ACC_WARPS && lane == 0) {
+    // producer: one stage = one K slice of one offset
+    for (int u = 0; u < units; ++u) {
+      const int s = u % TC_NSTG;
+      const uint32_t ph = (uint32_t)((u / TC_NSTG) & 1);
+      if (!tc_wait(&empty[s], ph ^ 1u)) {
+        atomicExch(&g_tc_error, 1);
+        *(volatile int*)&abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      const int i = vlist[u / NA], a = u % NA;
+      const int o = A.m2l_off[cls * A.count + i];
+      const int ox = (o & 255) - 128, oy = ((o >> 8) & 255) - 128, oz = ((o >> 16) & 255) - 128;
+      const int sc = ((cx + ox) & 1) | (((cy + oy) & 1) << 1) | (((cz + oz) & 1) << 2);
+      const int sx = hx0 + ((cx + ox) >> 1), sy = hy0 + ((cy + oy) >> 1), sz = hz0 + ((cz + oz) >> 1);
+      unsigned char* st = smem + (size_t)s * stage_bytes;
+      const int slot = A.m2l_slot[cls * A.count + i];
+      const float* img = A.img + (((int64_t)(level - A.lmin) * A.box_cells + slot) * 2 * NA + a) * A.Npad * 32;
+      tc_expect_tx(&full[s], stage_bytes);
+      tc_tma5(st, &maps.xh[level], 32 * a, sx, sy, sz, sc, &full[s]);
+      tc_tma5(st + xbytes, &maps.xl[level], 32 * a, sx, sy, sz, sc, &full[s]);
+      tc_bulk_g2s(st + 2 * xbytes, img, bbytes, &full[s]);
+      tc_bulk_g2s(st + 2 * xbytes + bbytes, img + (int64_t)NA * A.Npad * 32, bbytes, &full[s]);
+    }
+  } else if (warp == TC_ACC_WARPS + 1 && lane == 0) {
+    // MMA issuer: chunks of TC_CHUNK offsets into alternating TMEM buffers
+    for (int u = 0; u < units; ++u) {
+      const int g = u / cunits, buf = g & 1;
+      const uint32_t dt = tmem + (uint32_t)(buf * 128);
+      const bool first = (u % cunits) == 0;
+      if (first && g >= 2 && !tc_wait(&drained[buf], (uint32_t)(((g >> 1) - 1) & 1))) {
+        atomicExch(&g_tc_error, 1);
+        *(volatile int*)&abort_flag = 1;
+        break;
+      }
+      const int s = u % TC_NSTG;
+      const uint32_t ph = (uint32_t)((u / TC_NSTG) & 1);
+      if (!tc_wait(&full[s], ph)) {
+        atomicExch(&g_tc_error, 1);
+        *(volatile int*)&abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const int a = u % NA;
+      const int kvalid = min(32, twoP - 32 * a);  // K of this slice
+      const uint32_t st = sa(smem + (size_t)s * stage_bytes);
+      const uint32_t xh = st, xl = st + xbytes, bh = st + 2 * xbytes, bl = st + 2 * xbytes + bbytes;
+      uint32_t acc = first ? 0u : 1u;
+      for (int kk = 0; kk < kvalid; kk += 8) {
+        const uint32_t ko = (uint32_t)kk * 4;
+        tc_mma(dt, tc_desc(xh + ko), tc_desc(bh + ko), idesc, acc);
+        acc = 1;
+        tc_mma(dt, tc_desc(xh + ko), tc_desc(bl + ko), idesc, 1);
+        tc_mma(dt, tc_desc(xl + ko), tc_desc(bh + ko), idesc, 1);
+      }
+      tc_commit(&empty[s]);  // the stage is free once these MMAs have read it
+      if ((u + 1) % cunits == 0 || u + 1 == units) tc_commit(&ready[buf]);  // chunk complete
+    }
+  } else if (warp < TC_ACC_WARPS) {
+    // accumulator warps: TMEM lane r = brick cell r; each chunk is added to
+    // FP32 registers (round to nearest), so no tensor-core accumulation chain
+    // is longer than one chunk
+    float sum[TC_MAX_NPAD];
+#pragma unroll
+    for (int c = 0; c < TC_MAX_NPAD; ++c) sum[c] = 0.f;
+    bool good = true;
+    for (int g = 0; g < nchunks; ++g) {
+      const int buf = g & 1;
+      if (!tc_wait(&ready[buf], (uint32_t)((g >> 1) & 1))) {
+        atomicExch(&g_tc_error, 1);
+        *(volatile int*)&abort_flag = 1;
+        good = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 128);
+#pragma unroll
+      for (int c0 = 0; c0 < TC_MAX_NPAD; c0 += 16) {
+        if (c0 < A.Npad) {
+          float v[16];
+          tc_ld16(ta + (uint32_t)c0, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sum[c0 + j] += v[j];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc_arrive(&drained[buf]);
+    }
+    if (good) {
+      const int r = warp * 32 + lane;
+      const int dx = r % BX, dy = (r / BX) % BY, dz = r / (BX * BY);
+      const int X = 2 * (hx0 + dx) + cx, Y = 2 * (hy0 + dy) + cy, Z = 2 * (hz0 + dz) + cz;
+      const int64_t cell = A.level_off[level] + (int64_t)morton_encode(X, Y, Z);
+      if (A.flags[cell] & A.tgt_set) {
+        float* dst = A.part ? A.part + (int64_t)blockIdx.y * A.part_stride + cell * twoP : A.Lc + cell * twoP;
+        const bool add = A.part ? false : A.accumulate != 0;
+#pragma unroll
+        for (int c = 0; c < TC_MAX_NPAD; ++c)
+          if (c < twoP) dst[c] = add ? dst[c] + sum[c] : sum[c];
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (*(volatile int*)&abort_flag && tid == 0) {
+    // give copies and MMAs in flight a bounded time to land before the
+    // shared memory and TMEM are released
+    for (int s = 0; s < TC_NSTG; ++s) {
+      tc_wait(&full[s], 0);
+      tc_wait(&empty[s], 0);
+    }
+    tc_wait(&ready[0], 0);
+    tc_wait(&ready[1], 0);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
+// L = (L +) sum over splits of the partial rows, for the target cells of the
+// tensor-core levels
+__global__ void k_tc_reduce(const float* __restrict__ part, int64_t part_stride, int nsplit,
+                            const int* __restrict__ flags, int64_t off0, int64_t ncell, int twoP, int tgt_set,
+                            int accumulate, float* __restrict__ Lc, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ncell * twoP) return;
+  const int64_t cell = off0 + e / twoP;
+  if (!(flags[cell] & tgt_set)) return;
+  const int64_t i = off0 * twoP + e;
+  float v = part[i];
+  for (int k = 1; k < nsplit; ++k) v += part[k * part_stride + i];
+  Lc[i] = accumulate ? Lc[i] + v : v;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+}  // namespace
+
+struct fmm_tc_state {
+  int ready = 0;
+  int NA = 0, Npad = 0;
+  float* img = nullptr;
+  float* xh = nullptr;
+  float* xl = nullptr;
+  int64_t lat_off[HFMM_MAX_LEVEL + 1] = {};  // float offset of each level in xh / xl
+  TcMaps maps;
+};
+
+void m2l_tc_release(fmm_tree* t) {
+  delete t->m2l_tcore;  // its device buffers belong to the handle's allocation list
+  t->m2l_tcore = nullptr;
+}
+
+// lowest level served by the tensor-core M2L (0: none): FP32 form, even P
+// (rows of 16-byte multiples), 2P <= 256 (one MMA N), class lattices of at
+// least 8 x 8 x 8 cells (levels >= 4), class lists held in shared memory
+int m2l_tc_lmin(const fmm_tree* t) {
+  if (!t->use_m2l_tcore || t->precision != HFMM_FP32 || (t->P & 1) || 2 * t->P > 256 ||
+      t->m2l_count > TC_MAX_COUNT || t->L < 4)
+    return 0;
+  return 4;
+}
+
+static int tc_prepare(fmm_tree* t, cudaStream_t s) {
+  if (t->m2l_tcore && t->m2l_tcore->ready) return HFMM_OK;
+  const int lmin = m2l_tc_lmin(t);
+  if (!lmin) return HFMM_ERR_UNSUPPORTED;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return HFMM_ERR_UNSUPPORTED;
+  if (!t->m2l_tcore) t->m2l_tcore = new (std::nothrow) fmm_tc_state();
+  if (!t->m2l_tcore) return HFMM_ERR_NOMEM;
+  fmm_tc_state& S = *t->m2l_tcore;
+  const int P = t->P, twoP = 2 * P, L = t->L;
+  S.NA = (twoP + 31) / 32;
+  S.Npad = (twoP + 15) / 16 * 16;
+  // operator images
+  const int64_t nslot = (int64_t)(L - lmin + 1) * t->box_cells;
+  const int64_t img_floats = nslot * 2 * S.NA * S.Npad * 32;
+  HFMM_TRY(tree_alloc(t, (void**)&S.img, sizeof(float) * img_floats));
+  const int64_t nel = nslot * S.NA * S.Npad * 32;
+  k_tc_ops<<<ceil_div(nel, 256), 256, 0, s>>>(t->op_m2l32, P, t->box_cells, lmin, L, S.NA, S.Npad, S.img);
+  count_launches(1);
+  HFMM_TRY(hfmm_last_launch());
+  // lattice arrays and their tensor maps
+  int64_t tot = 0;
+  for (int l = lmin; l <= L; ++l) {
+    S.lat_off[l] = tot;
+    tot += ((int64_t)1 << (3 * l)) * twoP;
+  }
+  HFMM_TRY(tree_alloc(t, (void**)&S.xh, sizeof(float) * tot));
+  HFMM_TRY(tree_alloc(t, (void**)&S.xl, sizeof(float) * tot));
+  for (int l = lmin; l <= L; ++l) {
+    const cuuint64_t hh = (cuuint64_t)1 << (l - 1);
+    const cuuint64_t dims[5] = {(cuuint64_t)twoP, hh, hh, hh, 8};
+    const cuuint64_t row = (cuuint64_t)twoP * sizeof(float);
+    const cuuint64_t strides[4] = {row, row * hh, row * hh * hh, row * hh * hh * hh};
+    const cuuint32_t box[5] = {32, BX, BY, BZ, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    for (int w = 0; w < 2; ++w) {
+      float* base = (w ? S.xl : S.xh) + S.lat_off[l];
+      CUresult r = enc(w ? &S.maps.xl[l] : &S.maps.xh[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dims, strides,
+                       box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return HFMM_ERR_UNSUPPORTED;
+    }
+  }
+  S.ready = 1;
+  return HFMM_OK;
+}
+
+// Far field of levels lmin..L on the tensor cores; *nlaunch = kernels launched
+int m2l_tc_stage(fmm_tree* t, int src_set, int tgt_set, int accumulate, cudaStream_t s, int* nlaunch) {
+  *nlaunch = 0;
+  HFMM_TRY(tc_prepare(t, s));
+  fmm_tc_state& S = *t->m2l_tcore;
+  const int lmin = m2l_tc_lmin(t), L = t->L, P = t->P, twoP = 2 * P;
+  const float* M = reinterpret_cast<const float*>(t->M);
+  for (int l = lmin; l <= L; ++l) {
+    const int64_t n = ((int64_t)1 << (3 * l)) * twoP;
+    k_tc_split<<<ceil_div(n, 256), 256, 0, s>>>(M, t->flags, t->level_off[l], l, twoP, src_set, S.xh + S.lat_off[l],
+                                                S.xl + S.lat_off[l], t->skip);
+    ++*nlaunch;
+  }
+  TcArgs A;
+  A.img = S.img;
+  A.m2l_off = t->m2l_off;
+  A.m2l_slot = t->m2l_box_index;
+  A.flags = t->flags;
+  A.level_off = t->level_off_dev;
+  A.Lc = reinterpret_cast<float*>(t->Lc);
+  A.skip = t->skip;
+  A.count = t->m2l_count;
+  A.box_cells = t->box_cells;
+  A.P = P;
+  A.NA = S.NA;
+  A.Npad = S.Npad;
+  A.lmin = lmin;
+  A.L = L;
+  A.tgt_set = tgt_set;
+  A.accumulate = accumulate;
+  int nb = 0;
+  for (int l = 0; l <= HFMM_MAX_LEVEL + 1; ++l) A.brick_first[l] = 0;
+  for (int l = lmin; l <= L; ++l) {
+    A.brick_first[l] = nb;
+    const int h = 1 << (l - 1);
+    nb += 8 * (h / BX) * (h / BY) * (h / BZ);
+  }
+  A.brick_first[L + 1] = nb;
+  // split the offset lists until the grid covers the GPU about twice
+  const int nsplit = std::max(1, std::min(t->m2l_part_max, (2 * 152 + nb - 1) / nb));
+  A.part = nsplit > 1 ? reinterpret_cast<float*>(t->m2l_part) : nullptr;
+  A.part_stride = t->total_cells * (int64_t)twoP;
+  const size_t stage_bytes = 2 * (size_t)(BX * BY * BZ * 128) + 2 * (size_t)S.Npad * 128;
+  const size_t smem = TC_NSTG * stage_bytes + 1024;
+  HFMM_TRY(set_smem_any((const void*)k_m2l_tc, smem));
+  k_m2l_tc<<<dim3(nb, nsplit), TC_THREADS, smem, s>>>(S.maps, A);
+  ++*nlaunch;
+  if (nsplit > 1) {
+    const int64_t off0 = t->level_off[lmin];
+    const int64_t ncell = t->level_off[L] + ((int64_t)1 << (3 * L)) - off0;
+    k_tc_reduce<<<ceil_div(ncell * twoP, 256), 256, 0, s>>>(A.part, A.part_stride, nsplit, t->flags, off0, ncell,
+                                                            twoP, tgt_set, accumulate, A.Lc, t->skip);
+    ++*nlaunch;
+  }
+  return hfmm_last_launch();
+}
+
+// nonzero when a bounded wait of the tensor-core M2L gave up (synchronises s);
+// clears the flag when asked
+int m2l_tc_error(cudaStream_t s, bool clear) {
+  int h = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return 1;
+  if (h && clear) {
+    int z = 0;
+    cudaMemcpyToSymbolAsync(g_tc_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+  }
+  return h;
+}

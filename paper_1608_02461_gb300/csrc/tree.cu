@@ -779,6 +779,15 @@ int build_m2l_tiles(fmm_tree* t, cudaStream_t s) {
     t->m2l_cells[i] = cells + i * cstride;
     t->m2l_tiles[i] = tiles + i * tstride;
     t->m2l_ntiles[i] = nt[i];
+    // tiles are in level order: count those below each level
+    std::vector<int4> ht(nt[i]);
+    if (nt[i] > 0)
+      HFMM_CUDA_TRY(cudaMemcpy(ht.data(), t->m2l_tiles[i], sizeof(int4) * nt[i], cudaMemcpyDeviceToHost));
+    for (int l = 0; l <= HFMM_MAX_LEVEL + 1; ++l) {
+      int c = 0;
+      for (const int4& tl : ht) c += tl.x < l ? 1 : 0;
+      t->m2l_tiles_lt[i][l] = c;
+    }
   }
   return HFMM_OK;
 }

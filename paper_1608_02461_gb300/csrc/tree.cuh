@@ -13,6 +13,7 @@ struct DevBuf {
 };
 
 struct fmm_tree_ext;  // solver workspaces (capi.cu)
+struct fmm_tc_state;  // tensor-core M2L state (m2l_tc.cu)
 
 // kernels launched by the library (all handles)
 void count_launches(int64_t n);
@@ -163,6 +164,7 @@ struct fmm_tree {
   int* m2l_cells[3] = {nullptr, nullptr, nullptr};
   int4* m2l_tiles[3] = {nullptr, nullptr, nullptr};
   int m2l_ntiles[3] = {0, 0, 0};
+  int m2l_tiles_lt[3][HFMM_MAX_LEVEL + 2] = {};  // tiles of the levels below l, per target mask
   // per (target mask, source mask) pair, index 3 (tm-1) + (sm-1): the valid
   // offsets of every tile (built on first use)
   int* m2l_vlist[9] = {};
@@ -212,6 +214,12 @@ struct fmm_tree {
   //      instead of evaluating Bessel and Legendre functions per apply
   void* rtab = nullptr;
   int use_rtab = 1;
+
+  // ---- tensor-core M2L (FP32 form, levels >= 4): operator images, class
+  //      lattices of the multipoles and their TMA descriptors, built on first
+  //      use; use_m2l_tcore: 0 off, 1 passes with volume targets, 2 all passes
+  fmm_tc_state* m2l_tcore = nullptr;
+  int use_m2l_tcore = 1;
 
   // ---- near field concurrent with the far field: P2P runs on its own
   //      stream (fork/join through events, also inside captured graphs) into
@@ -319,6 +327,14 @@ int fmm_core_adjoint(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
 int fmm_core_dk(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
 // HFMM_ERR_TIMEOUT (or 0) recorded by a kernel's bounded wait; synchronises s
 int fmm_device_error(cudaStream_t s, bool clear);
+// raises a kernel's dynamic shared-memory limit (never lowers it)
+int set_smem_any(const void* fn, size_t bytes);
+
+// m2l_tc.cu: tensor-core M2L of the levels >= m2l_tc_lmin(t) (0: not available)
+int m2l_tc_lmin(const fmm_tree* t);
+int m2l_tc_stage(fmm_tree* t, int src_set, int tgt_set, int accumulate, cudaStream_t s, int* nlaunch);
+int m2l_tc_error(cudaStream_t s, bool clear);
+void m2l_tc_release(fmm_tree* t);
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cudaStream_t s);
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, float2* phi_bnd, cudaStream_t s);
 int fmm_scatter_from(fmm_tree* t, const void* sorted, int tgt_set, double2* phi_vol, double2* phi_bnd,

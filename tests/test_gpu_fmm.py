@@ -276,3 +276,32 @@ def test_concurrent_near_field_is_bitwise_equal(prec):
     xa, ia = a.gmres(rhs, **kw)
     xb, ib = b.gmres(rhs, **kw)
     assert ia.iters == ib.iters and torch.equal(xa, xb)
+
+
+@pytest.mark.parametrize("p", [6, 8])
+def test_tensor_core_m2l_matches_cuda_core(p):
+    """The FP32 form's far field at levels >= 4 on the tensor cores (tcgen05,
+    TF32 inputs split hi + lo, three products) against the CUDA-core M2L of
+    the same form and against the FP64 form: both within the FP32 bound."""
+    n, k, leaf = 32, 9.0, 8  # L = 4
+    tc = hfmm.Tree(n, k, p, 0.4, leaf, "fp32")
+    cc = _tree_with_env({"HFMM_M2L_TC": "0"}, n, k, p, 0.4, leaf, "fp32")
+    f64 = hfmm.Tree(n, k, p, 0.4, leaf, "fp64")
+    assert tc.stats().L == 4
+    qv = inputs.complex_normal(n ** 3, 21)
+    qb = inputs.complex_normal(6 * n * n, 22)
+    for src, tgt in [(3, 1), (3, 3), (1, 1)]:
+        a = run_apply(tc, qv if src & 1 else None, qb if src & 2 else None, src, tgt)
+        b = run_apply(cc, qv if src & 1 else None, qb if src & 2 else None, src, tgt)
+        c = run_apply(f64, qv if src & 1 else None, qb if src & 2 else None, src, tgt)
+        assert rel(a, c) < 3e-5, (src, tgt, rel(a, c))
+        assert rel(b, c) < 3e-5
+    # repeated applies are bitwise identical (fixed summation order)
+    a2 = run_apply(tc, qv, qb, 3, 3)
+    assert np.array_equal(a2, run_apply(tc, qv, qb, 3, 3))
+    # and the preconditioned solve converges like the CUDA-core form
+    rhs = torch.from_numpy(inputs.rhs("uniform_real", n, 4)).to(DEV)
+    kw = dict(restart=30, rtol=1e-6, inner_rtol=1e-2, inner_maxit=20, inner_m=20)
+    _, it = tc.gmres(rhs, **kw)
+    _, ic = cc.gmres(rhs, **kw)
+    assert it.status == 0 and it.relres_true < 1e-6 and abs(it.iters - ic.iters) <= 1
