@@ -1789,11 +1789,13 @@ __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restri
 // persistent (two per SM in FP32, so that one block's leaf setup overlaps the
 // other's sums) and take target leaves in turn.  Per pair: one broadcast read
 // of the staged source {q, lin}, one table read and a complex multiply-add;
-// no transcendental functions.  As in k_p2p_v2, each target is served by tpt
-// threads summing strided shares of a window of staged sources (consecutive
-// sources of a leaf are consecutive lattice nodes, so the table reads of a
-// warp fall in distinct banks); FP32 window sums are added with Kahan
-// compensation.  KMODE 0: G; 1: conj(G) (adjoint).
+// no transcendental functions.  In FP32 a thread holds four consecutive
+// targets, so each staged-source read (a 16-byte load, which the shared
+// memory serves a quarter warp at a time) feeds four pairs; tpt threads per
+// group of targets sum strided shares of a window of staged sources
+// (consecutive sources of a leaf are consecutive lattice nodes, so the table
+// reads of a warp fall in distinct banks); FP32 window sums are added with
+// Kahan compensation.  KMODE 0: G; 1: conj(G) (adjoint).
 template <typename T> struct LatSrc;
 template <> struct LatSrc<float> { float4 v; };                       // q.x, q.y, lin (bits), 0
 template <> struct LatSrc<double> { double2 q; int lin; int pad[3]; };
@@ -1905,16 +1907,26 @@ __global__ void __launch_bounds__(LAT_THREADS, sizeof(T) == 4 ? 2 : 1)
     __syncthreads();
     const int nnb = n_nb;
     const int total = nb_pre[nnb];
+    // NT consecutive targets per thread share each source read; tpt threads
+    // per group of NT targets take strided shares of the window
+    constexpr int NT = sizeof(T) == 4 ? 4 : 1;
+    const int nq = (ntgt + NT - 1) / NT;
     int tpt = 1;
-    while (tpt < 32 && (tpt * 2) * ntgt <= LAT_THREADS) tpt *= 2;
-    const int tslots = LAT_THREADS / tpt;
+    while (tpt < 32 && (tpt * 2) * nq <= LAT_THREADS) tpt *= 2;
+    const int qslots = LAT_THREADS / tpt;
     const int sub = tid & (tpt - 1);
-    for (int tb = 0; tb < ntgt; tb += tslots) {
-      const int ti = tb + tid / tpt;
-      const bool active = ti < ntgt;
-      const int i = tlo + (active ? ti : 0);
-      const int lt = lin[i];
-      C<T> tot = mkc<T>(0, 0), comp = mkc<T>(0, 0);
+    for (int qb = 0; qb < nq; qb += qslots) {
+      const int qi = qb + tid / tpt;
+      const bool active = qi < nq;
+      int lt[NT];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int ti = NT * qi + j;
+        lt[j] = lin[tlo + ((active && ti < ntgt) ? ti : 0)];
+      }
+      C<T> tot[NT], comp[NT];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) tot[j] = comp[j] = mkc<T>(0, 0);
       for (int wb = 0; wb < total; wb += LAT_WS) {
         const int wn = min(LAT_WS, total - wb);
         __syncthreads();
@@ -1930,45 +1942,62 @@ __global__ void __launch_bounds__(LAT_THREADS, sizeof(T) == 4 ? 2 : 1)
           lat_stage(ssrc[e], d.qs[j], lin[j]);
         }
         __syncthreads();
-        C<T> part = mkc<T>(0, 0);
+        C<T> part[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) part[j] = mkc<T>(0, 0);
         if (active) {
-#pragma unroll 8
+#pragma unroll 4
           for (int e = sub; e < wn; e += tpt) {
             C<T> q;
             int ls;
             lat_read(ssrc[e], q, ls);
-            const C<T> g = stab[abs(lt - ls)];
-            if constexpr (KMODE == 0) {
-              part.x = fma(g.x, q.x, fma(-g.y, q.y, part.x));
-              part.y = fma(g.x, q.y, fma(g.y, q.x, part.y));
-            } else {
-              part.x = fma(g.x, q.x, fma(g.y, q.y, part.x));
-              part.y = fma(g.x, q.y, fma(-g.y, q.x, part.y));
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+              const C<T> g = stab[abs(lt[j] - ls)];
+              if constexpr (KMODE == 0) {
+                part[j].x = fma(g.x, q.x, fma(-g.y, q.y, part[j].x));
+                part[j].y = fma(g.x, q.y, fma(g.y, q.x, part[j].y));
+              } else {
+                part[j].x = fma(g.x, q.x, fma(g.y, q.y, part[j].x));
+                part[j].y = fma(g.x, q.y, fma(-g.y, q.x, part[j].y));
+              }
             }
           }
         }
-        if constexpr (sizeof(T) == 4) {
-          const T yx = part.x - comp.x, yy = part.y - comp.y;
-          const T tx = tot.x + yx, ty = tot.y + yy;
-          comp.x = (tx - tot.x) - yx;
-          comp.y = (ty - tot.y) - yy;
-          tot.x = tx;
-          tot.y = ty;
-        } else {
-          tot = cadd<T>(tot, part);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          if constexpr (sizeof(T) == 4) {
+            const T yx = part[j].x - comp[j].x, yy = part[j].y - comp[j].y;
+            const T tx = tot[j].x + yx, ty = tot[j].y + yy;
+            comp[j].x = (tx - tot[j].x) - yx;
+            comp[j].y = (ty - tot[j].y) - yy;
+            tot[j].x = tx;
+            tot[j].y = ty;
+          } else {
+            tot[j] = cadd<T>(tot[j], part[j]);
+          }
         }
       }
-      for (int o = tpt >> 1; o > 0; o >>= 1) {
-        tot.x += __shfl_xor_sync(0xffffffffu, tot.x, o);
-        tot.y += __shfl_xor_sync(0xffffffffu, tot.y, o);
-      }
+#pragma unroll
+      for (int j = 0; j < NT; ++j)
+        for (int o = tpt >> 1; o > 0; o >>= 1) {
+          tot[j].x += __shfl_xor_sync(0xffffffffu, tot[j].x, o);
+          tot[j].y += __shfl_xor_sync(0xffffffffu, tot[j].y, o);
+        }
       if (active && sub == 0) {
-        const bool is_vol = i < d.leaf_mid[leaf];
-        if ((is_vol && (src_set & HFMM_SET_VOL)) || (!is_vol && (src_set & HFMM_SET_BND))) {
-          const double2 sg = is_vol ? sig_vol : sig_bnd;  // conjugated by the caller in adjoint mode
-          cfma<T>(tot, mkc<T>(T(sg.x), T(sg.y)), d.qs[i]);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const int ti = NT * qi + j;
+          if (ti >= ntgt) break;
+          const int i = tlo + ti;
+          C<T> v = tot[j];
+          const bool is_vol = i < d.leaf_mid[leaf];
+          if ((is_vol && (src_set & HFMM_SET_VOL)) || (!is_vol && (src_set & HFMM_SET_BND))) {
+            const double2 sg = is_vol ? sig_vol : sig_bnd;  // conjugated by the caller in adjoint mode
+            cfma<T>(v, mkc<T>(T(sg.x), T(sg.y)), d.qs[i]);
+          }
+          p2p_store<T>(d, i, v);
         }
-        p2p_store<T>(d, i, tot);
       }
     }
   }

@@ -507,34 +507,40 @@ __global__ void k_lat_max_offset(const int* __restrict__ box, int L, const int* 
   atomicMax(dmax, m);
 }
 
-__global__ void k_lat_lin(const double* __restrict__ xyz, int64_t n, double inv_h, int W, int* __restrict__ lin) {
+__global__ void k_lat_lin(const double* __restrict__ xyz, int64_t n, double inv_h, int Sy, int Sz,
+                          int* __restrict__ lin) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int cx = (int)llrint(xyz[3 * i] * inv_h), cy = (int)llrint(xyz[3 * i + 1] * inv_h),
             cz = (int)llrint(xyz[3 * i + 2] * inv_h);
-  lin[i] = (cz * W + cy) * W + cx;
+  lin[i] = cx + Sy * cy + Sz * cz;
 }
 
-// half table over delta = (dz W + dy) W + dx >= 0 (dx, dy, dz in [-D, D]):
-// G(h d) = e^{i k h |d|} / (4 pi h |d|) (the 3D Green's function of Sec. 5.2 on the lattice), zero at d = 0
-__global__ void k_lat_table(int D, double h, double k, int64_t nhalf, int64_t npad, double2* __restrict__ t64,
-                            float2* __restrict__ t32) {
-  const int W = 2 * D + 1;
+// signed residue of r modulo m in [-(m/2), m - m/2)
+__device__ __forceinline__ int64_t balanced_mod(int64_t r, int64_t m) {
+  int64_t v = ((r % m) + m) % m;
+  if (v >= m - m / 2) v -= m;
+  return v;
+}
+
+// half table over delta = dx + Sy dy + Sz dz >= 0 (dx, dy, dz in [-D, D],
+// Sy > 2D, Sz = (2D + 1) Sy): G(h d) = e^{i k h |d|} / (4 pi h |d|) (the 3D
+// Green's function of Sec. 5.2 on the lattice), zero at d = 0 and at codes
+// that no offset of the box produces
+__global__ void k_lat_table(int D, int Sy, int Sz, double h, double k, int64_t nhalf, int64_t npad,
+                            double2* __restrict__ t64, float2* __restrict__ t32) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= npad) return;
   double2 g = make_double2(0.0, 0.0);
   if (e < nhalf) {
-    // balanced base-W digits of e
-    int64_t r = e;
-    int dx = (int)(((r % W) + W) % W);
-    if (dx > D) dx -= W;
-    r = (r - dx) / W;
-    int dy = (int)(((r % W) + W) % W);
-    if (dy > D) dy -= W;
-    r = (r - dy) / W;
-    const int dz = (int)r;
-    const int d2 = dx * dx + dy * dy + dz * dz;
-    if (d2 > 0) {
+    const int64_t dx = balanced_mod(e, Sy);
+    const int64_t r = (e - dx) / Sy;  // dy + (Sz / Sy) dz
+    const int64_t W = Sz / Sy;
+    const int64_t dy = balanced_mod(r, W);
+    const int64_t dz = (r - dy) / W;
+    const bool inbox = dx >= -D && dx <= D && dy >= -D && dy <= D && dz >= -D && dz <= D;
+    const int64_t d2 = dx * dx + dy * dy + dz * dz;
+    if (inbox && d2 > 0) {
       const double rr = h * sqrt((double)d2);
       double sn, cs;
       sincos(k * rr, &sn, &cs);
@@ -829,21 +835,30 @@ int build_lattice_table(fmm_tree* t, cudaStream_t s) {
   HFMM_CUDA_TRY(cudaMemcpyAsync(&D, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
   HFMM_CUDA_TRY(cudaStreamSynchronize(s));
   cudaFreeAsync(box, s);
+  // strides of the offset code: Sy > 2D with Sy = 12 (mod 16), so that a
+  // 4 x 4 patch of lattice nodes (a half-warp's sources) reads 16 distinct
+  // 8-byte banks of the table; Sz = (2D + 1) Sy keeps the code one-to-one
   const int W = 2 * D + 1;
-  const int64_t nhalf = ((int64_t)W * W * W + 1) / 2;
+  int Sy = W;
+  while (Sy % 16 != 12) ++Sy;
+  const int Sz = W * Sy;
+  const int64_t nhalf = (int64_t)D * (1 + Sy + Sz) + 1;
   const int64_t npad = (nhalf + 1) / 2 * 2;  // multiple of 16 bytes in both precisions
+  const int64_t maxc = (int64_t)(t->n + 1) * (1 + Sy + Sz);
   // the table is staged whole in shared memory by the near-field kernel
-  if (D < 1 || npad * (int64_t)sizeof(float2) > HFMM_LAT_TABLE_MAX_BYTES) return HFMM_OK;
+  if (D < 1 || npad * (int64_t)sizeof(float2) > HFMM_LAT_TABLE_MAX_BYTES || maxc >= (1ll << 31))
+    return HFMM_OK;
   HFMM_TRY(tree_alloc_t(t, &t->lat_lin, t->n_pts));
   HFMM_TRY(tree_alloc_t(t, &t->lat_tab32, npad));
   HFMM_TRY(tree_alloc_t(t, &t->lat_tab64, npad));
-  k_lat_lin<<<ceil_div(t->n_pts, 256), 256, 0, s>>>(t->xyz, t->n_pts, inv_h, W, t->lat_lin);
-  k_lat_table<<<ceil_div(npad, 256), 256, 0, s>>>(D, t->h, t->k, nhalf, npad, t->lat_tab64, t->lat_tab32);
+  k_lat_lin<<<ceil_div(t->n_pts, 256), 256, 0, s>>>(t->xyz, t->n_pts, inv_h, Sy, Sz, t->lat_lin);
+  k_lat_table<<<ceil_div(npad, 256), 256, 0, s>>>(D, Sy, Sz, t->h, t->k, nhalf, npad, t->lat_tab64, t->lat_tab32);
   HFMM_TRY(hfmm_last_launch());
   t->lat_half = npad;
   // FP64: table, window of 32-byte staged sources and 4 KB of static shared memory
   t->lat_tab64_fits = npad * (int64_t)sizeof(double2) + (int64_t)HFMM_LAT_WS * 32 + 4096 <= HFMM_SMEM_MAX;
   t->lat_D = D;
-  t->lat_W = W;
+  t->lat_Sy = Sy;
+  t->lat_Sz = Sz;
   return HFMM_OK;
 }

@@ -198,11 +198,12 @@ struct fmm_tree {
   //      the lattice h Z^3, so the kernel between two points depends only on
   //      their integer offset d in [-D, D]^3 (D: largest offset component
   //      between points of near leaves), coded as delta = lin_t - lin_s with
-  //      lin = (iz W + iy) W + ix, W = 2D + 1; G(d) = G(-d), so a half table
-  //      lat_tab[|delta|] = e^{ik h|d|} / (4 pi h|d|) (0 at d = 0) holds all
+  //      lin = ix + Sy iy + Sz iz (Sy > 2D, Sz = (2D + 1) Sy: one-to-one on
+  //      the box); G(d) = G(-d), so a half table lat_tab[|delta|] =
+  //      e^{ik h|d|} / (4 pi h|d|) (0 at d = 0) holds all
   int lat_D = 0;                // 0: no table
-  int lat_W = 0;                // 2 lat_D + 1
-  int64_t lat_half = 0;         // (W^3 + 1) / 2 entries, padded to a multiple of 16 bytes (FP64 size)
+  int lat_Sy = 0, lat_Sz = 0;   // strides of the offset code
+  int64_t lat_half = 0;         // D (1 + Sy + Sz) + 1 entries, padded to a multiple of 16 bytes (FP64 size)
   int* lat_lin = nullptr;       // [n_pts] lin of each sorted point
   float2* lat_tab32 = nullptr;  // [lat_half] FP32 table
   double2* lat_tab64 = nullptr; // [lat_half] FP64 table
