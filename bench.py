@@ -52,7 +52,7 @@ P2P_SMEM_PEAK_TFLOPS = 152 * 2.070e9 * 32 / 3 * P2P_FLOP_PER_PAIR / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_p2p_lat launch (ncu,
 # 64^3 k=16 p=6 FP32 workload) for the three passes of the preconditioner:
 # volume -> boundary, boundary -> boundary, all -> volume
-P2P_DRAM_BYTES = {"A": 2604288, "B": 505600, "C": 5680384}
+P2P_DRAM_BYTES = {"A": 2616832, "B": 520704, "C": 5701888}
 L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 
 
