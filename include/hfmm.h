@@ -218,7 +218,8 @@ int hfmm_fdm_apply(fmm_tree* tree, const void* d_u, void* d_out, void* stream);
  * gmres_solve -- Sec. 3-4, Sec. 6: flexible right-preconditioned restarted
  * GMRES(m) for A x = b with A the 7-point operator of the tree's (n, k) and
  * M^-1 = fmm_precond_apply.  Classical Gram-Schmidt with reorthogonalisation,
- * complex Givens rotations, FP64 throughout the Krylov arithmetic.
+ * complex Givens rotations, FP64 Krylov arithmetic (the preconditioner's
+ * inner boundary solve runs in the precision of the tree's FMM form).
  *   d_b     n^3 complex128 right-hand side
  *   d_x     in: initial guess x0; out: solution (written also when the
  *           status is NOT_CONVERGED)
@@ -228,6 +229,25 @@ int hfmm_fdm_apply(fmm_tree* tree, const void* d_u, void* d_out, void* stream);
  */
 int gmres_solve(fmm_tree* tree, const void* d_b, void* d_x,
                 const hfmm_gmres_params* gp, hfmm_gmres_info* info, void* stream);
+
+/*
+ * bicgstab_solve -- Sec. 3 (and its GMRES/BiCGSTAB comparison figure):
+ * right-preconditioned BiCGSTAB (van der Vorst) for the same system and
+ * preconditioner as gmres_solve, FP64 complex vectors.  One iteration
+ * applies A and M^-1 twice (once each when it stops at the half step);
+ * stops when ||b - A x|| < rtol ||b|| by the recurrence residual, or on a
+ * breakdown (rho = 0 or omega = 0).
+ *   d_b, d_x  as in gmres_solve (d_x holds x0 on entry)
+ *   gp        rtol, maxit (iterations; 0: 500) and the preconditioner's
+ *             inner_rtol, inner_maxit, inner_m; restart_m is not used
+ *   info      iters = BiCGSTAB iterations, restarts = preconditioner
+ *             applications, history[i] = relative residual after iteration i,
+ *             relres_true = ||b - A x|| / ||b|| recomputed at exit
+ * Returns HFMM_OK when converged, HFMM_ERR_NOT_CONVERGED otherwise (x and
+ * info written), or another error.
+ */
+int bicgstab_solve(fmm_tree* tree, const void* d_b, void* d_x,
+                   const hfmm_gmres_params* gp, hfmm_gmres_info* info, void* stream);
 
 /*
  * gmres_solve_batched -- many independent solves of gmres_solve (Sec. 3-4,

@@ -35,6 +35,7 @@ struct fmm_tree_ext {
   GmresWorkT<float> inner32;    // the complex64 boundary solve of the FP32 form
   GmresWorkT<float> inner_g32;  // the same in the graph form
   GmresWork outer;   // A x = b
+  BicgWork bicg;     // A x = b by BiCGSTAB
   PrecGraph pg;
 };
 
@@ -268,6 +269,7 @@ extern "C" void fmm_destroy_tree(fmm_tree* tree) {
   gmres_work_free(e->inner32);
   gmres_work_free(e->inner_g32);
   gmres_work_free(e->outer);
+  bicg_work_free(e->bicg);
   prec_graph_drop(e->pg);
   if (e->pg.cap) cudaStreamDestroy(e->pg.cap);
   release(tree);
@@ -514,6 +516,61 @@ extern "C" int gmres_solve(fmm_tree* t, const void* d_b, void* d_x, const hfmm_g
   if (info) {
     info->iters = R.iters;
     info->restarts = R.restarts;
+    info->inner_iters_total = inner_total;
+    info->relres_est = R.relres_est;
+    info->relres_true = R.relres_true;
+    info->status = st != HFMM_OK ? st : (R.converged ? HFMM_OK : HFMM_ERR_NOT_CONVERGED);
+  }
+  if (st != HFMM_OK) return st;
+  return R.converged ? HFMM_OK : HFMM_ERR_NOT_CONVERGED;
+}
+
+extern "C" int bicgstab_solve(fmm_tree* t, const void* d_b, void* d_x, const hfmm_gmres_params* gp,
+                              hfmm_gmres_info* info, void* stream) {
+  if (!t || !d_b || !d_x || !gp) return HFMM_ERR_INVALID_ARG;
+  if (!t->lattice) return HFMM_ERR_UNSUPPORTED;
+  if (!(gp->rtol > 0.0) || gp->maxit < 0 || !(gp->inner_rtol > 0.0) || gp->inner_maxit < 1 || gp->inner_m < 1 ||
+      gp->inner_m > 500)
+    return HFMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  fmm_tree_ext* e = ext_of(t);
+  HFMM_TRY(bicg_work_reserve(e->bicg, t->n_vol));
+  DevOp A = [t, s](const double2* in, double2* out) -> int {
+    t->timer.begin(HFMM_STAGE_FDM, s);
+    int st = fdm_apply_dev(t->n, t->h, t->k, in, out, s);
+    t->timer.end(1, s);
+    return st;
+  };
+  int inner_total = 0;
+  const bool graphs = t->use_graphs && gp->inner_m >= gp->inner_maxit;
+  PrecGraph& G = e->pg;
+  if (graphs && G.flags) HFMM_CUDA_TRY(cudaMemsetAsync(G.flags + 2, 0, sizeof(int), s));
+  G.eager_its = 0;
+  DevOp M = [t, gp, s, graphs, &inner_total](const double2* in, double2* out) -> int {
+    if (graphs) return precond_graph(t, in, out, gp->inner_rtol, gp->inner_maxit, s);
+    int its = 0;
+    int st = precond_impl(t, in, out, gp->inner_rtol, gp->inner_maxit, gp->inner_m, &its, s);
+    inner_total += its;
+    return st;
+  };
+  const int maxit = gp->maxit > 0 ? gp->maxit : 500;
+  BicgResult R;
+  int st = bicgstab_run(e->bicg, A, &M, (const double2*)d_b, (double2*)d_x, gp->rtol, maxit, false, &R,
+                        info ? info->history : nullptr, info ? info->history_len : 0, s);
+  if (graphs && st == HFMM_OK && G.flags) {
+    int tot = 0;
+    HFMM_CUDA_TRY(cudaMemcpyAsync(&tot, G.flags + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    inner_total = tot;
+    if (G.pending) {
+      t->timer.resolve_slots(G.slots);
+      G.pending = false;
+    }
+    if (fmm_device_error(s, true)) st = HFMM_ERR_TIMEOUT;
+  }
+  if (info) {
+    info->iters = R.iters;
+    info->restarts = R.precond_applies;
     info->inner_iters_total = inner_total;
     info->relres_est = R.relres_est;
     info->relres_true = R.relres_true;

@@ -7,6 +7,7 @@
 // rotations and the least-squares solution are FP64 in both cases.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 
 #include "krylov.cuh"
 #include "tree.cuh"
@@ -609,6 +610,208 @@ int gmres_cycle_device(GmresWorkT<R>& W, const DevOpT<R>& A, const C<R>* b, C<R>
   k_count_add<<<1, 1, 0, s>>>(d_jdone, d_total);
   count_launches(3);
   return hfmm_last_launch();
+}
+
+// ---------------------------------------------------------------- BiCGSTAB
+
+namespace {
+
+// p = r + beta (p - omega v)
+__global__ void k_bicg_p(double2* __restrict__ p, const double2* __restrict__ r, const double2* __restrict__ v,
+                         double2 beta, double2 omega, int64_t N) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const double2 pe = p[e], ve = v[e], re = r[e];
+  const double2 d = make_double2(pe.x - (omega.x * ve.x - omega.y * ve.y), pe.y - (omega.x * ve.y + omega.y * ve.x));
+  p[e] = make_double2(re.x + beta.x * d.x - beta.y * d.y, re.y + beta.x * d.y + beta.y * d.x);
+}
+
+// out = a - c b
+__global__ void k_bicg_sub(double2* __restrict__ out, const double2* __restrict__ a, const double2* __restrict__ b,
+                           double2 c, int64_t N) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const double2 ae = a[e], be = b[e];
+  out[e] = make_double2(ae.x - (c.x * be.x - c.y * be.y), ae.y - (c.x * be.y + c.y * be.x));
+}
+
+// x += alpha phat + omega shat; r = s - omega t (r may be null: x only)
+__global__ void k_bicg_x(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ phat,
+                         const double2* __restrict__ shat, const double2* __restrict__ sv,
+                         const double2* __restrict__ t, double2 alpha, double2 omega, int64_t N) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const double2 ph = phat[e];
+  double2 xe = x[e];
+  xe.x += alpha.x * ph.x - alpha.y * ph.y;
+  xe.y += alpha.x * ph.y + alpha.y * ph.x;
+  if (shat) {
+    const double2 sh = shat[e];
+    xe.x += omega.x * sh.x - omega.y * sh.y;
+    xe.y += omega.x * sh.y + omega.y * sh.x;
+  }
+  x[e] = xe;
+  if (r) {
+    const double2 se = sv[e], te = t[e];
+    r[e] = make_double2(se.x - (omega.x * te.x - omega.y * te.y), se.y - (omega.x * te.y + omega.y * te.x));
+  }
+}
+
+}  // namespace
+
+int bicg_work_reserve(BicgWork& W, int64_t N) {
+  if (W.base && W.N == N) return HFMM_OK;
+  bicg_work_free(W);
+  W.N = N;
+  const size_t vec = (size_t)N * sizeof(double2);
+  const size_t vb = (vec + 255) / 256 * 256;
+  const size_t bytes = 8 * vb + (size_t)RMAXB * 4 * sizeof(double2) + 256 + 4 * 256;
+  if (cudaMalloc(&W.base, bytes) != cudaSuccess) {
+    W.base = nullptr;
+    return HFMM_ERR_NOMEM;
+  }
+  if (cudaMallocHost((void**)&W.host, 8 * sizeof(double)) != cudaSuccess) {
+    cudaFree(W.base);
+    W.base = nullptr;
+    return HFMM_ERR_NOMEM;
+  }
+  char* q = (char*)W.base;
+  double2** vecs[8] = {&W.r, &W.rhat, &W.p, &W.v, &W.s, &W.t, &W.phat, &W.shat};
+  for (int i = 0; i < 8; ++i) {
+    *vecs[i] = (double2*)q;
+    q += vb;
+  }
+  W.partial = (double2*)q;
+  q += (size_t)RMAXB * 4 * sizeof(double2);
+  W.counter = (unsigned*)q;
+  q += 256;
+  W.dots = (double2*)q;  // [0] dot, [1] norm in .x
+  if (cudaMemset(W.counter, 0, 256) != cudaSuccess) {
+    bicg_work_free(W);
+    return HFMM_ERR_CUDA;
+  }
+  return HFMM_OK;
+}
+
+void bicg_work_free(BicgWork& W) {
+  if (W.base) cudaFree(W.base);
+  if (W.host) cudaFreeHost(W.host);
+  W = BicgWork();
+}
+
+// <a, b> = sum conj(a) b and, when want_norm, ||b||; read back to the host
+static int bicg_dot(BicgWork& W, const double2* a, const double2* b, bool want_norm, std::complex<double>* dot,
+                    double* nrm, cudaStream_t s) {
+  const int64_t N = W.N;
+  k_cgs<0, double><<<red_blocks(N), RT, 0, s>>>(a, N, a ? 1 : 0, nullptr, const_cast<double2*>(b), N, W.partial,
+                                                W.counter, W.dots, want_norm ? (double*)(W.dots + 1) : nullptr,
+                                                nullptr, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                nullptr, nullptr, nullptr, 0.0);
+  count_launches(1);
+  HFMM_TRY(hfmm_last_launch());
+  HFMM_CUDA_TRY(cudaMemcpyAsync(W.host, W.dots, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (dot) *dot = std::complex<double>(W.host[0], W.host[1]);
+  if (nrm) *nrm = W.host[2];
+  return HFMM_OK;
+}
+
+static inline double2 d2(std::complex<double> z) { return make_double2(z.real(), z.imag()); }
+
+int bicgstab_run(BicgWork& W, const DevOp& A, const DevOp* M, const double2* b, double2* x, double rtol, int maxit,
+                 bool x0_zero, BicgResult* res, double* history, int history_len, cudaStream_t s) {
+  using cd = std::complex<double>;
+  const int64_t N = W.N;
+  const unsigned gN = ceil_div(N, 256);
+  BicgResult R;
+  double bnorm = 0.0;
+  HFMM_TRY(bicg_dot(W, nullptr, b, true, nullptr, &bnorm, s));
+  if (!std::isfinite(bnorm)) return HFMM_ERR_NONFINITE;
+  if (bnorm == 0.0) {
+    HFMM_CUDA_TRY(cudaMemsetAsync(x, 0, N * sizeof(double2), s));
+    R.converged = 1;
+    if (res) *res = R;
+    return HFMM_OK;
+  }
+  if (x0_zero) {
+    HFMM_CUDA_TRY(cudaMemcpyAsync(W.r, b, N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  } else {
+    HFMM_TRY(A(x, W.v));
+    k_bicg_sub<<<gN, 256, 0, s>>>(W.r, b, W.v, make_double2(1.0, 0.0), N);
+    count_launches(1);
+  }
+  double rn = 0.0;
+  HFMM_TRY(bicg_dot(W, nullptr, W.r, true, nullptr, &rn, s));
+  double relres = rn / bnorm;
+  if (relres < rtol) R.converged = 1;
+  HFMM_CUDA_TRY(cudaMemcpyAsync(W.rhat, W.r, N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(W.p, 0, N * sizeof(double2), s));
+  HFMM_CUDA_TRY(cudaMemsetAsync(W.v, 0, N * sizeof(double2), s));
+  cd rho_old(1.0, 0.0), alpha(1.0, 0.0), omega(1.0, 0.0);
+  for (int it = 1; it <= maxit && !R.converged && !R.breakdown; ++it) {
+    R.iters = it;
+    cd rho;
+    HFMM_TRY(bicg_dot(W, W.rhat, W.r, false, &rho, nullptr, s));
+    if (rho == cd(0.0, 0.0)) {
+      R.breakdown = 1;
+      break;
+    }
+    const cd beta = it == 1 ? cd(0.0, 0.0) : (rho / rho_old) * (alpha / omega);
+    k_bicg_p<<<gN, 256, 0, s>>>(W.p, W.r, W.v, d2(beta), d2(it == 1 ? cd(0.0, 0.0) : omega), N);
+    count_launches(1);
+    const double2* ph = W.p;
+    if (M) {
+      HFMM_TRY((*M)(W.p, W.phat));
+      ph = W.phat;
+      R.precond_applies++;
+    }
+    HFMM_TRY(A(ph, W.v));
+    cd rv;
+    HFMM_TRY(bicg_dot(W, W.rhat, W.v, false, &rv, nullptr, s));
+    alpha = rho / rv;
+    k_bicg_sub<<<gN, 256, 0, s>>>(W.s, W.r, W.v, d2(alpha), N);
+    count_launches(1);
+    double sn = 0.0;
+    HFMM_TRY(bicg_dot(W, nullptr, W.s, true, nullptr, &sn, s));
+    if (!std::isfinite(sn)) return HFMM_ERR_NONFINITE;
+    if (sn / bnorm < rtol) {  // half step
+      k_bicg_x<<<gN, 256, 0, s>>>(x, nullptr, ph, nullptr, nullptr, nullptr, d2(alpha), make_double2(0, 0), N);
+      count_launches(1);
+      relres = sn / bnorm;
+      if (history && it - 1 < history_len) history[it - 1] = relres;
+      R.converged = 1;
+      break;
+    }
+    const double2* sh = W.s;
+    if (M) {
+      HFMM_TRY((*M)(W.s, W.shat));
+      sh = W.shat;
+      R.precond_applies++;
+    }
+    HFMM_TRY(A(sh, W.t));
+    cd ts, tt;
+    HFMM_TRY(bicg_dot(W, W.t, W.s, false, &ts, nullptr, s));
+    HFMM_TRY(bicg_dot(W, W.t, W.t, false, &tt, nullptr, s));
+    omega = tt != cd(0.0, 0.0) ? ts / tt : cd(0.0, 0.0);
+    k_bicg_x<<<gN, 256, 0, s>>>(x, W.r, ph, sh, W.s, W.t, d2(alpha), d2(omega), N);
+    count_launches(1);
+    HFMM_TRY(bicg_dot(W, nullptr, W.r, true, nullptr, &rn, s));
+    relres = rn / bnorm;
+    if (!std::isfinite(relres)) return HFMM_ERR_NONFINITE;
+    if (history && it - 1 < history_len) history[it - 1] = relres;
+    rho_old = rho;
+    if (relres < rtol) R.converged = 1;
+    else if (omega == cd(0.0, 0.0)) R.breakdown = 1;
+  }
+  R.relres_est = relres;
+  // true residual
+  HFMM_TRY(A(x, W.v));
+  k_bicg_sub<<<gN, 256, 0, s>>>(W.r, b, W.v, make_double2(1.0, 0.0), N);
+  count_launches(1);
+  HFMM_TRY(bicg_dot(W, nullptr, W.r, true, nullptr, &rn, s));
+  R.relres_true = rn / bnorm;
+  if (res) *res = R;
+  return HFMM_OK;
 }
 
 #define HFMM_KRYLOV_INSTANTIATE(R)                                                                        \

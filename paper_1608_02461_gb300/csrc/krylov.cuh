@@ -70,3 +70,28 @@ int dev_norm(GmresWorkT<R>& W, const C<R>* x, int64_t N, double* out_dev, cudaSt
 template <typename R>
 int gmres_cycle_device(GmresWorkT<R>& W, const DevOpT<R>& A, const C<R>* b, C<R>* x, int m, double rtol,
                        int* d_done, int* d_jdone, int* d_total, cudaStream_t s);
+
+// Right-preconditioned BiCGSTAB (van der Vorst), FP64 complex vectors: the
+// paper's Sec. 3 short-recurrence alternative to GMRES.  Two operator and two
+// preconditioner applications per iteration (one of each when it stops at
+// the half step); scalars on the host.
+struct BicgWork {
+  int64_t N = 0;
+  double2 *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
+  double2 *phat = nullptr, *shat = nullptr;
+  double2* partial = nullptr;  // reduction partials
+  unsigned* counter = nullptr; // blocks finished in the current reduction launch
+  double2* dots = nullptr;     // [0] inner product, [1].x norm
+  double* host = nullptr;      // pinned mirror of dots
+  void* base = nullptr;
+};
+
+struct BicgResult {
+  int iters = 0, converged = 0, breakdown = 0, precond_applies = 0;
+  double relres_est = 0, relres_true = 0;
+};
+
+int bicg_work_reserve(BicgWork& W, int64_t N);
+void bicg_work_free(BicgWork& W);
+int bicgstab_run(BicgWork& W, const DevOp& A, const DevOp* M, const double2* b, double2* x, double rtol, int maxit,
+                 bool x0_zero, BicgResult* res, double* history, int history_len, cudaStream_t s);

@@ -81,6 +81,9 @@ SIGNATURES = {
     "gmres_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.POINTER(hfmm_gmres_params),
                                    ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
+    "bicgstab_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.POINTER(hfmm_gmres_params),
+                                      ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
     "fmm_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hfmm_stats)]),
     "fmm_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "gmres_solve_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -247,6 +250,26 @@ class Tree:
                                _stream_ptr(stream))
         if st != HFMM_OK and (st != HFMM_ERR_NOT_CONVERGED or raise_on_nonconvergence):
             raise HfmmError(st, "gmres_solve")
+        gi = GmresInfo(info.iters, info.restarts, info.inner_iters_total, info.status,
+                       info.relres_est, info.relres_true, list(hist[:min(info.iters, history_len)]))
+        return x, gi
+
+    def bicgstab(self, b, x=None, rtol=1e-6, maxit=0, inner_rtol=1e-4, inner_maxit=200, inner_m=50,
+                 history_len=2000, raise_on_nonconvergence=False, stream=None):
+        """bicgstab_solve: right-preconditioned BiCGSTAB with the FMM
+        preconditioner.  Returns (x, GmresInfo) with iters = BiCGSTAB
+        iterations and restarts = preconditioner applications."""
+        torch = _torch()
+        _dev_c128(b, self.n_vol, "b")
+        if x is None:
+            x = torch.zeros_like(b)
+        gp = hfmm_gmres_params(1, rtol, maxit, inner_rtol, inner_maxit, inner_m)
+        hist = (ctypes.c_double * history_len)()
+        info = hfmm_gmres_info(0, 0, 0, 0, 0.0, 0.0, hist, history_len)
+        st = lib().bicgstab_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(gp), ctypes.byref(info),
+                                  _stream_ptr(stream))
+        if st != HFMM_OK and (st != HFMM_ERR_NOT_CONVERGED or raise_on_nonconvergence):
+            raise HfmmError(st, "bicgstab_solve")
         gi = GmresInfo(info.iters, info.restarts, info.inner_iters_total, info.status,
                        info.relres_est, info.relres_true, list(hist[:min(info.iters, history_len)]))
         return x, gi

@@ -1,9 +1,11 @@
-"""Writes tests/golden/oracle_<workload>.json: the FP64 CPU oracle's own
-preconditioned GMRES solve of a workload (iteration counts, residual history,
-true residual).  Calls only oracle/ and the seeded input module; nothing here
-comes from the CUDA path.
+"""Writes tests/golden/oracle_<workload>.json (GMRES) or
+tests/golden/oracle_bicgstab_<workload>.json (--method bicgstab): the FP64 CPU
+oracle's own preconditioned solve of a workload (iteration counts, residual
+history, true residual).  Calls only oracle/ and the seeded input module;
+nothing here comes from the CUDA path.
 
 Usage: python tests/golden/make_golden.py helmholtz_n64_k16_p6 [--inner-rtol 1e-2 --inner-maxit 20]
+       [--method gmres|bicgstab]
 """
 import argparse
 import json
@@ -15,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
-from oracle import bem, fdm, gmres  # noqa: E402
+from oracle import bem, bicgstab, fdm, gmres  # noqa: E402
 from paper_1608_02461_gb300 import inputs  # noqa: E402
 
 
@@ -24,6 +26,7 @@ def main():
     ap.add_argument("workload")
     ap.add_argument("--inner-rtol", type=float, default=1e-2)
     ap.add_argument("--inner-maxit", type=int, default=20)
+    ap.add_argument("--method", choices=("gmres", "bicgstab"), default="gmres")
     a = ap.parse_args()
     w = inputs.WORKLOADS[a.workload]
     n, k = w["n"], w["k"]
@@ -40,8 +43,15 @@ def main():
         log.flush()
         return z
 
-    x, info = gmres.fgmres(lambda u: fdm.fdm_apply(u, n, k), b, M, m=w["restart"], rtol=1e-6)
+    A = lambda u: fdm.fdm_apply(u, n, k)
+    if a.method == "gmres":
+        x, info = gmres.fgmres(A, b, M, m=w["restart"], rtol=1e-6)
+    else:
+        x, info = bicgstab.bicgstab(A, b, M, rtol=1e-6, maxit=500)
+        info["restarts"] = info["precond_applies"]
+        info["relres_est"] = info["history"][-1] if info["history"] else 0.0
     out = {
+        "method": a.method,
         "source": "oracle/ (FP64 CPU), written by tests/golden/make_golden.py",
         "workload": a.workload, **{key: w[key] for key in ("n", "k", "p", "leaf", "theta", "restart")},
         "rtol": 1e-6, "inner_rtol": a.inner_rtol, "inner_maxit": a.inner_maxit, "inner_m": a.inner_maxit,
@@ -50,7 +60,8 @@ def main():
         "relres_est": info["relres_est"], "relres_true": info["relres_true"], "history": info["history"],
         "wall_s": time.time() - t0,
     }
-    json.dump(out, open(os.path.join(HERE, f"oracle_{a.workload}.json"), "w"), indent=1)
+    name = f"oracle_{a.workload}.json" if a.method == "gmres" else f"oracle_bicgstab_{a.workload}.json"
+    json.dump(out, open(os.path.join(HERE, name), "w"), indent=1)
     print(json.dumps({k2: v for k2, v in out.items() if k2 not in ("history", "inner_iters")}))
 
 

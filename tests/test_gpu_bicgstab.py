@@ -1,0 +1,105 @@
+"""GPU right-preconditioned BiCGSTAB (bicgstab_solve) against the oracle's
+BiCGSTAB: the recorded FP64 oracle solves (tests/golden/), a live oracle
+solve on a small grid (iterates agree), the FP32 form, the graph form of the
+preconditioner, and the not-converged status."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bem, bicgstab, fdm  # noqa: E402
+from paper_1608_02461_gb300 import hfmm, inputs  # noqa: E402
+
+DEV = "cuda:0"
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(workload):
+    path = os.path.join(GOLDEN, f"oracle_bicgstab_{workload}.json")
+    if not os.path.exists(path):
+        pytest.skip("recorded oracle solve not present")
+    return json.load(open(path))
+
+
+@pytest.mark.parametrize("workload", ["helmholtz_n16_k4_p4"])
+def test_bicgstab_matches_recorded_oracle_solve(workload):
+    g = _golden(workload)
+    w = inputs.WORKLOADS[workload]
+    b = torch.from_numpy(inputs.workload_rhs(workload)).to(DEV)
+    kw = dict(rtol=g["rtol"], inner_rtol=g["inner_rtol"], inner_maxit=g["inner_maxit"], inner_m=g["inner_m"])
+    t = hfmm.Tree(w["n"], w["k"], w["p"], w["theta"], w["leaf"], "fp64")
+    x, info = t.bicgstab(b, **kw)
+    assert info.status == 0 and info.relres_true < g["rtol"]
+    assert abs(info.iters - g["iters"]) <= 1, (info.iters, g["iters"])
+    assert abs(info.restarts - g["restarts"]) <= 2  # preconditioner applications
+    # the FP32 form: converges within two more iterations
+    t32 = hfmm.Tree(w["n"], w["k"], w["p"], w["theta"], w["leaf"], "fp32")
+    _, i32 = t32.bicgstab(b, **kw)
+    assert i32.status == 0 and i32.relres_true < g["rtol"] and i32.iters <= g["iters"] + 2
+
+
+def test_bicgstab_iterates_match_live_oracle():
+    n, k, p, leaf = 8, 3.0, 4, 8
+    pr = bem.Problem(n, k, p, leaf, 0.4)
+    rng = np.random.default_rng(3)
+    bh = rng.uniform(-1, 1, n ** 3) + 1j * rng.uniform(-1, 1, n ** 3)
+    A = lambda u: fdm.fdm_apply(u, n, k)
+    M = lambda r: pr.precond(r, inner_rtol=1e-10, inner_maxit=200, inner_m=200)[0]
+    xo, io = bicgstab.bicgstab(A, bh, M, rtol=1e-9)
+    t = hfmm.Tree(n, k, p, 0.4, leaf, "fp64")
+    x, info = t.bicgstab(torch.from_numpy(bh).to(DEV), rtol=1e-9, inner_rtol=1e-10, inner_maxit=200,
+                         inner_m=200)
+    assert info.status == 0 and io["converged"]
+    assert info.iters == io["iters"]
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-7
+    np.testing.assert_allclose(info.history, io["history"], rtol=1e-4, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bicgstab_graph_equals_host_driven(prec):
+    n, k = 12, 5.0
+    b = torch.from_numpy(inputs.rhs("uniform_real", n, 9)).to(DEV)
+    tg = hfmm.Tree(n, k, 6, 0.4, 16, prec)
+    th = hfmm.Tree(n, k, 6, 0.4, 16, prec)
+    th.use_graphs(False)
+    kw = dict(rtol=1e-6, inner_rtol=1e-2, inner_maxit=20, inner_m=20)
+    xg, ig = tg.bicgstab(b, **kw)
+    xh, ih = th.bicgstab(b, **kw)
+    assert ig.iters == ih.iters and ig.restarts == ih.restarts
+    assert torch.equal(xg, xh)
+
+
+def test_bicgstab_not_converged_status():
+    n, k = 10, 4.0
+    t = hfmm.Tree(n, k, 4, 0.4, 8, "fp64")
+    b = torch.from_numpy(inputs.rhs("uniform_real", n, 2)).to(DEV)
+    x, info = t.bicgstab(b, rtol=1e-14, maxit=1, inner_rtol=1e-2, inner_maxit=10, inner_m=10)
+    assert info.status == hfmm.HFMM_ERR_NOT_CONVERGED and info.iters == 1
+    assert 0 < info.relres_true < 1
+    with pytest.raises(hfmm.HfmmError):
+        t.bicgstab(b, rtol=1e-14, maxit=1, inner_rtol=1e-2, inner_maxit=10, inner_m=10,
+                   raise_on_nonconvergence=True)
+
+
+def test_bicgstab_full_size_converges_with_a_near_fixed_preconditioner():
+    """64^3, k = 16: BiCGSTAB assumes a fixed preconditioner; with the inner
+    boundary solve to 1e-4 it converges (FP64 and FP32 forms alike), while
+    GMRES (flexible) needs fewer preconditioner applications."""
+    name = "helmholtz_n64_k16_p6"
+    w = inputs.WORKLOADS[name]
+    b = torch.from_numpy(inputs.workload_rhs(name)).to(DEV)
+    kw = dict(rtol=1e-6, maxit=60, inner_rtol=1e-4, inner_maxit=120, inner_m=120)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        t = hfmm.Tree(w["n"], w["k"], w["p"], w["theta"], w["leaf"], prec)
+        _, i = t.bicgstab(b, **kw)
+        _, g = t.gmres(b, restart=50, rtol=1e-6, inner_rtol=1e-4, inner_maxit=120, inner_m=120)
+        assert i.status == 0 and i.relres_true < 1e-6 and g.status == 0
+        assert g.iters < i.restarts  # GMRES applies the preconditioner fewer times
+        res[prec] = i.iters
+    assert abs(res["fp32"] - res["fp64"]) <= 2
