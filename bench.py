@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-solve batched measurement")
     ap.add_argument("--no-bicgstab", action="store_true", help="skip the BiCGSTAB solve of the same system")
     ap.add_argument("--batched-maxit", type=int, default=200)
+    ap.add_argument("--sweep", choices=("kh", "p"),
+                    help="print one JSON line per point of a sweep (fixed kh = 0.3125 over n, or the "
+                         "expansion order p at n = 31, k = 10) instead of the benchmark line")
     ap.add_argument("--apply-only", nargs=2, type=int, metavar=("SRC", "TGT"),
                     help="profiling case: build the tree and run two FMM applies with these "
                          "source/target set masks (1 volume, 2 boundary, 3 both), print nothing else")
@@ -513,11 +516,47 @@ def run_apply_only(args):
     tree.close()
 
 
+def run_sweep(args):
+    """GMRES iterations and time of the preconditioned solve along one sweep;
+    inner boundary solve to 1e-4 (at most 200 steps) so that the FMM
+    accuracy, not the inner solve, sets the outer iteration count."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_1608_02461_gb300 import hfmm, inputs
+    dev = torch.device("cuda:0")
+    if args.sweep == "kh":
+        points = [dict(q, p=inputs.SWEEP_KH_P, prec="fp32") for q in inputs.SWEEP_KH]
+    else:
+        sp = inputs.SWEEP_P
+        points = [dict(n=sp["n"], k=sp["k"], p=p, prec="fp64") for p in sp["ps"]]
+    for q in points:
+        n = q["n"]
+        t = hfmm.Tree(n, q["k"], q["p"], 0.4, 32 if n < 32 else 64, q["prec"])
+        b = torch.from_numpy(inputs.rhs("uniform_real", n, 6)).to(dev)
+        kw = dict(restart=30, rtol=1e-6, inner_rtol=1e-4, inner_maxit=200, inner_m=200)
+        t.gmres(b, **kw)  # warm-up (builds the preconditioner graph)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, info = t.gmres(b, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"sweep": args.sweep, "n": n, "k": q["k"], "kh": q["k"] / (n + 1), "p": q["p"],
+                          "precision": q["prec"], "gmres_iters": info.iters,
+                          "inner_iters_total": info.inner_iters_total, "relres_true": info.relres_true,
+                          "time_s": e0.elapsed_time(e1) * 1e-3, "converged": info.status == 0}), flush=True)
+        t.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.apply_only:
         run_apply_only(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

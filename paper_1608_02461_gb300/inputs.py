@@ -30,10 +30,22 @@ WORKLOADS = {
     # FP32 form at scale
     "helmholtz_n128_k32_p8": dict(n=128, k=32.0, p=8, leaf=64, theta=0.35, restart=50,
                                   rhs="complex_normal", seed=3),
+    # smallest point of the fixed-kh sweep (kh = 0.3125), small enough for the oracle
+    "helmholtz_n15_k5_p8": dict(n=15, k=5.0, p=8, leaf=32, theta=0.4, restart=30,
+                                rhs="uniform_real", seed=6),
     # free-space volume FMM for the differentiable form
     "fmm_n64_k12_p6": dict(n=64, k=12.0, p=6, leaf=64, theta=0.4, restart=50,
                            rhs="complex_normal_unit", seed=5),
 }
+
+
+# Sweeps that mirror the paper's experiments in 3D (rhs uniform_real, seed 6):
+# fixed kh = 0.3125 with h = 1/(n+1) halved and k doubled (the paper's
+# (h, kappa) = (2^-4, 5) ... (2^-7, 40) table), and the expansion order p at
+# fixed (n, k) (the paper's accuracy-vs-iterations figure).
+SWEEP_KH = [dict(n=15, k=5.0), dict(n=31, k=10.0), dict(n=63, k=20.0), dict(n=127, k=40.0)]
+SWEEP_KH_P = 8
+SWEEP_P = dict(n=31, k=10.0, ps=[2, 3, 4, 5, 6, 7, 8, 10])
 
 
 def node_coords(n: int) -> np.ndarray:
