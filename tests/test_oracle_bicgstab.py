@@ -64,7 +64,7 @@ def test_bicgstab_iterates_match_scipy(cplx):
 def test_bicgstab_fmm_preconditioned_fdm():
     """On the FDM Helmholtz system the FMM preconditioner turns BiCGSTAB into
     a few iterations, like GMRES (two preconditioner applies per iteration)."""
-    n, k = 10, 4.0
+    n, k = 8, 4.0
     pr = bem.Problem(n, k, 4, 8, 0.4)
     rng = np.random.default_rng(8)
     b = rng.uniform(-1, 1, n ** 3) + 0j
