@@ -1,4 +1,5 @@
-"""The FMM potential as a differentiable torch operation.
+"""The FMM potential and the preconditioned Helmholtz solve as differentiable
+torch operations.
 
 phi = G~ q on the volume points of a tree (free-space sum with self terms, no
 boundary correction), G~ the truncated FMM operator of Sec. 5.1.2 for the
@@ -45,3 +46,42 @@ class HelmholtzFMM(torch.autograd.Function):
 def fmm_potential(q, k, tree):
     """phi = G~ q, differentiable in q (complex128) and k (float64 scalar tensor)."""
     return HelmholtzFMM.apply(q, k, tree)
+
+
+class HelmholtzSolve(torch.autograd.Function):
+    """x = A(k)^-1 b for the 7-point operator of the tree's grid, solved by
+    the FMM-preconditioned GMRES (gmres_solve).  For real k, A is real and
+    symmetric, so the adjoint system A^H lam = dL/dx is the forward system and
+    is solved the same way (the preconditioner changes the convergence, not
+    the solution):
+
+      dL/db = lam,    dL/dk = Re <lam, 2k x>     (dA/dk = -2k I)
+
+    with <u, v> = sum conj(u) v, in PyTorch's convention for complex tensors."""
+
+    @staticmethod
+    def forward(ctx, b, k, tree, kw):
+        if abs(float(k) - tree.k) > 1e-12 * max(1.0, abs(tree.k)):
+            raise ValueError("k must equal the wavenumber the tree was built for")
+        x, info = tree.gmres(b.contiguous(), raise_on_nonconvergence=True, **kw)
+        ctx.tree = tree
+        ctx.kw = kw
+        ctx.k = float(k)
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        (x,) = ctx.saved_tensors
+        lam, _ = ctx.tree.gmres(grad_x.contiguous(), raise_on_nonconvergence=True, **ctx.kw)
+        grad_b = lam if ctx.needs_input_grad[0] else None
+        grad_k = None
+        if ctx.needs_input_grad[1]:
+            grad_k = (lam.conj() * (2.0 * ctx.k) * x).real.sum().to(torch.float64)
+        return grad_b, grad_k, None, None
+
+
+def helmholtz_solve(b, k, tree, **gmres_kw):
+    """x = A(k)^-1 b (FMM-preconditioned GMRES), differentiable in b
+    (complex128) and k (float64 scalar tensor); gmres_kw go to Tree.gmres."""
+    return HelmholtzSolve.apply(b, k, tree, gmres_kw)

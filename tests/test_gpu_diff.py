@@ -127,3 +127,43 @@ def test_autograd_against_finite_differences():
     _, gq32, gk32 = _loss_and_grads(t32, q, phit, k)
     assert (torch.linalg.vector_norm(gq32 - gq) / torch.linalg.vector_norm(gq)).item() < 1e-4
     assert abs(gk32 - gk) <= 1e-4 * abs(gk)
+
+
+def test_gradient_through_the_solve():
+    """x = A(k)^-1 b through the FMM-preconditioned GMRES: dL/db against a
+    dense solve of the assembled 7-point matrix (independent of the FMM), and
+    dL/db, dL/dk against central differences of the GPU solve."""
+    from oracle import fdm
+    n, k, p = 6, 3.0, 4
+    kw = dict(restart=30, rtol=1e-12, inner_rtol=1e-10, inner_maxit=100, inner_m=100)
+    tree = hfmm.Tree(n, k, p, 0.4, 8, "fp64")
+    rng = np.random.default_rng(12)
+    b = torch.from_numpy(rng.standard_normal(n ** 3) + 1j * rng.standard_normal(n ** 3)).to(DEV)
+    xt = torch.from_numpy(rng.standard_normal(n ** 3) + 0j).to(DEV)
+    bb = b.clone().requires_grad_(True)
+    kk = torch.tensor(k, dtype=torch.float64, device=DEV, requires_grad=True)
+    x = differentiable.helmholtz_solve(bb, kk, tree, **kw)
+    L = ((x - xt).abs() ** 2).sum()
+    L.backward()
+    gb, gk = bb.grad.detach().cpu().numpy(), kk.grad.item()
+    # dense check: dL/db = A^-1 (2 (x - xt)) with A real symmetric
+    A = np.column_stack([fdm.fdm_apply(e, n, k) for e in np.eye(n ** 3, dtype=np.complex128)])
+    xd = np.linalg.solve(A, b.cpu().numpy())
+    gd = np.linalg.solve(A, 2 * (xd - xt.cpu().numpy()))
+    assert np.linalg.norm(gb - gd) / np.linalg.norm(gd) < 1e-8
+    # central differences along random directions, and in k
+    h = 1e-6
+
+    def loss(tr, bv):
+        xv, _ = tr.gmres(bv, **kw)
+        return ((xv - xt).abs() ** 2).sum().item()
+
+    for s in range(3):
+        d = torch.from_numpy(rng.standard_normal(n ** 3) + 1j * rng.standard_normal(n ** 3)).to(DEV)
+        fd = (loss(tree, b + h * d) - loss(tree, b - h * d)) / (2 * h)
+        an = torch.real(torch.vdot(bb.grad, d)).item()
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-9, (s, fd, an)
+    tp = hfmm.Tree(n, k + h, p, 0.4, 8, "fp64")
+    tm = hfmm.Tree(n, k - h, p, 0.4, 8, "fp64")
+    fdk = (loss(tp, b) - loss(tm, b)) / (2 * h)
+    assert abs(fdk - gk) <= 1e-6 * abs(gk), (fdk, gk)
