@@ -74,3 +74,21 @@ def test_invalid_arguments_rejected_without_gpu(built_lib):
     assert st == hfmm.HFMM_ERR_INVALID_ARG
     assert L.fmm_apply(None, 1, 1, None, None, None, None, 0, None) == hfmm.HFMM_ERR_INVALID_ARG
     assert L.gmres_solve(None, None, None, None, None, None) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.bicgstab_solve(None, None, None, None, None, None) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.fmm_precond_apply(None, None, None, 1e-2, 20, 20, None, None) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.fmm_autotune(None, None) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.fmm_use_graphs(None, 1) == hfmm.HFMM_ERR_INVALID_ARG
+
+
+def test_binding_prototypes_match_header_arity():
+    """Every prototype of the binding has as many arguments as the header's
+    declaration (a mismatch would pass garbage through ctypes)."""
+    import re as _re
+    from paper_1608_02461_gb300 import hfmm
+    src = open(os.path.join(ROOT, "include", "hfmm.h")).read()
+    src = _re.sub(r"/\*.*?\*/", "", src, flags=_re.S)
+    for name, (_, args) in hfmm.SIGNATURES.items():
+        m = _re.search(r"\b" + name + r"\s*\(([^;]*?)\)\s*;", src, _re.S)
+        assert m, name
+        params = [p for p in m.group(1).split(",") if p.strip() and p.strip() != "void"]
+        assert len(params) == len(args), (name, len(params), len(args))
