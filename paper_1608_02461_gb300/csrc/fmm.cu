@@ -2205,6 +2205,11 @@ int launch_p2p_lat(fmm_tree* t, const FmmDev<T>& d, int src_set, int tgt_set, do
   int per_sm = 0;
   HFMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LAT_THREADS, smem));
   if (per_sm < 1) return HFMM_ERR_UNSUPPORTED;
+  // boundary-only near field on the side stream (concurrent with the far
+  // field): one block per SM, so that the far-field kernels find shared
+  // memory next to it (with volume sources the near field is the larger part
+  // and keeps two)
+  if (d.near && !(src_set & HFMM_SET_VOL)) per_sm = 1;
   const int grid = std::min(na, per_sm * sm_count());
   kern<<<grid, LAT_THREADS, smem, s>>>(d, t->near_off, t->near_count, src_set, tgt_set, sv, sb,
                                        act_list(t, tgt_set, t->L), na,
