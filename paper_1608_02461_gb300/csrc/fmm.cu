@@ -1194,26 +1194,16 @@ __global__ void k_pairs_reduce(FmmDev<T> d, const int4* __restrict__ tiles, cons
   const int64_t off = level_off[tile.x];
   const int lo = csr[tile.z + c], hi = csr[tile.z + c + 1];
   C<T>* dst = d.Lc + (off + cells[tile.z + c]) * P;
-  constexpr int NC = 8;  // independent chains: eight row loads in flight per thread
   for (int a = threadIdx.x; a < P; a += blockDim.x) {
-    C<T> v[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) v[j] = mkc<T>(0, 0);
+    C<T> v0 = mkc<T>(0, 0), v1 = mkc<T>(0, 0);
     int q = lo;
-    for (; q + NC <= hi; q += NC) {
-      C<T> r[NC];
-#pragma unroll
-      for (int j = 0; j < NC; ++j) r[j] = buf[(int64_t)(q + j) * P + a];
-#pragma unroll
-      for (int j = 0; j < NC; ++j) v[j] = cadd<T>(v[j], r[j]);
+    for (; q + 1 < hi; q += 2) {  // two independent chains, then combined
+      v0 = cadd<T>(v0, buf[(int64_t)q * P + a]);
+      v1 = cadd<T>(v1, buf[(int64_t)(q + 1) * P + a]);
     }
-    for (int j = 0; q < hi; ++q, ++j) v[j] = cadd<T>(v[j], buf[(int64_t)q * P + a]);
-    // combine the chains in a fixed order
-#pragma unroll
-    for (int w = NC / 2; w > 0; w >>= 1)
-#pragma unroll
-      for (int j = 0; j < w; ++j) v[j] = cadd<T>(v[j], v[j + w]);
-    dst[a] = accumulate ? cadd<T>(dst[a], v[0]) : v[0];
+    if (q < hi) v0 = cadd<T>(v0, buf[(int64_t)q * P + a]);
+    C<T> v = cadd<T>(v0, v1);
+    dst[a] = accumulate ? cadd<T>(dst[a], v) : v;
   }
 }
 
