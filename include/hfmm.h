@@ -260,7 +260,9 @@ int bicgstab_solve(fmm_tree* tree, const void* d_b, void* d_x,
  *                                          must be distinct
  *   infos                                  optional host array [count]
  * Returns the first hard error, else HFMM_ERR_NOT_CONVERGED if any solve did
- * not converge, else HFMM_OK.  Blocks the calling thread until done.
+ * not converge or stopped on a non-finite value (infos[i].status is then
+ * HFMM_ERR_NOT_CONVERGED or HFMM_ERR_NONFINITE for that solve alone), else
+ * HFMM_OK.  Blocks the calling thread until done.
  */
 int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_x, int count,
                         const hfmm_gmres_params* gp, hfmm_gmres_info* infos, void* stream);

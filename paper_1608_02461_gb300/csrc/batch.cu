@@ -133,11 +133,14 @@ extern "C" int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_
     if (wstatus[w] != HFMM_OK && rc == HFMM_OK) rc = wstatus[w];
   }
   cudaEventDestroy(start);
-  // first hard error, else NOT_CONVERGED when any solve did not converge
+  // first hard error, else NOT_CONVERGED when any solve did not converge or
+  // broke down on a non-finite value (a numerical outcome of that solve alone,
+  // reported in its info; the other solves' results stand)
+  auto solve_failed = [](int st) { return st == HFMM_ERR_NOT_CONVERGED || st == HFMM_ERR_NONFINITE; };
   for (int i = 0; i < count && rc == HFMM_OK; ++i)
-    if (status[i] != HFMM_OK && status[i] != HFMM_ERR_NOT_CONVERGED) rc = status[i];
+    if (status[i] != HFMM_OK && !solve_failed(status[i])) rc = status[i];
   if (rc == HFMM_OK)
     for (int i = 0; i < count; ++i)
-      if (status[i] == HFMM_ERR_NOT_CONVERGED) rc = HFMM_ERR_NOT_CONVERGED;
+      if (solve_failed(status[i])) rc = HFMM_ERR_NOT_CONVERGED;
   return rc;
 }
