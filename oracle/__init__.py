@@ -19,6 +19,8 @@ Modules
   translations M2M / M2L / L2L operators (exact re-expansion, then truncation)
   fmm          P2M, M2M, M2L, L2L, L2P, P2P, self terms, direct sum
   bem          the BEM-coupled FMM preconditioner (Passes A, B, C)
+  dirichlet    inhomogeneous Dirichlet data: double-layer kernel and sums
+               (direct and dipole FMM), the FDM lift, the BEM solve with data
   fdm          the 7-point finite-difference Helmholtz operator
   gmres        flexible right-preconditioned restarted GMRES
 

@@ -132,3 +132,47 @@ def gaunt_table(p: int):
             vals = np.conj(Yall[ls * ls + ls + mu]) @ f
             gt[a, b, ls] = vals.real
     return gt
+
+
+def regular_grad_all(p: int, k: float, v):
+    """Cartesian gradient of R_n^m(v) = j_n(k|v|) Y_n^m(v/|v|) for n < p:
+    shape (3, p^2, npts).  Used for dipole sources (the normal derivative of
+    the source-side expansion, paper Sec. 5.2, Eq. (bem) second term).
+
+    Chain rule in spherical coordinates,
+      grad R = rho^ dR/drho + theta^ (1/rho) dR/dtheta + phi^ (1/(rho sin theta)) dR/dphi,
+    with dR/drho = k j_n'(k rho) Y (scipy's derivative), dY/dphi = i m Y and,
+    for Y ~ P_n^|m|(cos theta), the Legendre identity
+      (1 - x^2) dP_n^m/dx = (n + m) P_{n-1}^m - n x P_n^m,  x = cos theta,
+    so dP_n^m(cos theta)/dtheta = -((n + m) P_{n-1}^m - n x P_n^m) / sin theta.
+    Points on the polar axis (sin theta = 0) or at the centre are refused."""
+    v = np.atleast_2d(np.asarray(v, dtype=np.float64))
+    r, th, ph = cart2sph(v)
+    st, ct = np.sin(th), np.cos(th)
+    if np.any(r <= 0) or np.any(np.abs(st) < 1e-12):
+        raise ValueError("regular_grad_all: point at the centre or on the polar axis")
+    P = p * p
+    ns, ms = nm_of(P)
+    jn = sph_jn(ns[:, None], k * r[None, :])
+    djn = sp.spherical_jn(ns[:, None], k * r[None, :], derivative=True)
+    Y = ylm_all(p, th, ph)
+    dY = np.empty_like(Y)
+    for n in range(p):
+        for m in range(-n, n + 1):
+            am = abs(m)
+            norm = sqrt((2 * n + 1) / (4 * pi) * factorial(n - am) / factorial(n + am))
+            pn = sp.lpmv(am, n, ct)
+            pn1 = sp.lpmv(am, n - 1, ct) if n >= 1 and am <= n - 1 else 0.0 * ct
+            dp = -((n + am) * pn1 - n * ct * pn) / st
+            d = norm * dp * np.exp(1j * am * ph)
+            if m < 0:
+                d = (-1) ** am * np.conj(d)
+            dY[idx(n, m)] = d
+    dR_drho = k * djn * Y
+    dR_dth = jn * dY / r[None, :]
+    dR_dph = jn * (1j * ms[:, None]) * Y / (r * st)[None, :]
+    e_r = np.stack([st * np.cos(ph), st * np.sin(ph), ct])
+    e_t = np.stack([ct * np.cos(ph), ct * np.sin(ph), -st])
+    e_p = np.stack([-np.sin(ph), np.cos(ph), np.zeros_like(ph)])
+    return (e_r[:, None, :] * dR_drho[None] + e_t[:, None, :] * dR_dth[None]
+            + e_p[:, None, :] * dR_dph[None])
