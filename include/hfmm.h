@@ -58,6 +58,7 @@ extern "C" {
 #define HFMM_FWD 0       /* phi = G~ q                                   */
 #define HFMM_ADJ 1       /* phi = G~^H q  (conjugate transpose)          */
 #define HFMM_DK  2       /* phi = d(G~ q)/dk                             */
+#define HFMM_DLP 3       /* phi = D~ q  (double layer, boundary sources)  */
 
 typedef struct hfmm_params {
     int p;            /* expansion order: degrees 0..p-1 (1 <= p <= 16)  */
@@ -174,6 +175,15 @@ void fmm_destroy_tree(fmm_tree* tree);
  *             k-derivative of the truncated FMM (tangent of every stage:
  *             Bessel functions in P2M/L2P, translation operators, near-field
  *             kernel, self terms).
+ *   HFMM_DLP  phi = D~ q:        the double layer of Eq. (bem) (Sec. 5.2):
+ *             phi_i = sum_{j != i} q_j dG/dn_y(x_i, y_j),
+ *             dG/dn_y = (i k r - 1) e^{ikr} / (4 pi r^2) (y - x).n_y / r,
+ *             for boundary sources y_j (src_set must be HFMM_SET_BND) with
+ *             the outward normals of their faces; lattice trees only
+ *             (UNSUPPORTED otherwise).  The own panel contributes nothing
+ *             (it is flat: (y - x).n_y = 0); no jump term is added.  The
+ *             FMM is the same but for P2M (normal derivative of the regular
+ *             basis: dipole multipoles) and P2P (the kernel above).
  *
  *   src_set, tgt_set  non-zero OR of HFMM_SET_VOL / HFMM_SET_BND
  *   d_q_vol, d_q_bnd  input weights (complex128) per set of the input side;
@@ -206,6 +216,43 @@ int fmm_apply(fmm_tree* tree, int src_set, int tgt_set,
 int fmm_precond_apply(fmm_tree* tree, const void* d_r, void* d_z,
                       double inner_rtol, int inner_maxit, int inner_m,
                       int* inner_iters, void* stream);
+
+/*
+ * bem_solve_dirichlet -- the BEM solution of -Lap u - k^2 u = f in the cube
+ * with Dirichlet data u = u_Gamma on the boundary (Sec. 5.2-5.3: Eq. (ubound)
+ * for q = du/dn, then Eq. (uinter) at the interior nodes), every sum by the
+ * FMM:
+ *   g = G_{Gamma,Omega} (h^3 f) - u_Gamma / 2 - D_{Gamma,Gamma} (h^2 u_Gamma)
+ *   solve (-V) q = g                           (inner GMRES, as in
+ *                                               fmm_precond_apply)
+ *   u = G_{Omega,Omega} (h^3 f) + G_{Omega,Gamma} (h^2 q) + s_Omega f
+ *       - D_{Omega,Gamma} (h^2 u_Gamma)
+ * with D the double layer of fmm_apply's HFMM_DLP mode.  With u_Gamma = 0 it
+ * is fmm_precond_apply (r = f).  A starting iterate for gmres_solve on the
+ * system of hfmm_dirichlet_rhs.  Lattice trees only.
+ *   d_f        n^3 complex128 volume data (device)
+ *   d_u_bnd    6 n^2 complex128 Dirichlet values at the panel centres (device)
+ *   d_u        n^3 complex128 result (device, overwritten)
+ *   inner_rtol, inner_maxit, inner_m, inner_iters  as in fmm_precond_apply
+ * Errors: INVALID_ARG, UNSUPPORTED (explicit points), NOMEM, CUDA, TIMEOUT.
+ */
+int bem_solve_dirichlet(fmm_tree* tree, const void* d_f, const void* d_u_bnd, void* d_u,
+                        double inner_rtol, int inner_maxit, int inner_m,
+                        int* inner_iters, void* stream);
+
+/*
+ * hfmm_dirichlet_rhs -- right-hand side of the 7-point system (Sec. 2) with
+ * Dirichlet data: the stencil's neighbours outside the interior are the
+ * boundary grid nodes off the edges, i.e. the panel centres, so with
+ * u = u_Gamma there
+ *   b_i = f_i + (1/h^2) sum of u_Gamma over the boundary neighbours of node i
+ * and hfmm_fdm_apply(u) = b for the interior values u.  Lattice trees only.
+ *   d_f      n^3 complex128 (device)
+ *   d_u_bnd  6 n^2 complex128 (device), panel order as everywhere
+ *   d_b      n^3 complex128 result (device; may be d_f)
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ */
+int hfmm_dirichlet_rhs(fmm_tree* tree, const void* d_f, const void* d_u_bnd, void* d_b, void* stream);
 
 /*
  * hfmm_fdm_apply -- the 7-point operator of Sec. 2 (reading: -Lap - k^2):

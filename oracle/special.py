@@ -139,40 +139,43 @@ def regular_grad_all(p: int, k: float, v):
     shape (3, p^2, npts).  Used for dipole sources (the normal derivative of
     the source-side expansion, paper Sec. 5.2, Eq. (bem) second term).
 
-    Chain rule in spherical coordinates,
-      grad R = rho^ dR/drho + theta^ (1/rho) dR/dtheta + phi^ (1/(rho sin theta)) dR/dphi,
-    with dR/drho = k j_n'(k rho) Y (scipy's derivative), dY/dphi = i m Y and,
-    for Y ~ P_n^|m|(cos theta), the Legendre identity
-      (1 - x^2) dP_n^m/dx = (n + m) P_{n-1}^m - n x P_n^m,  x = cos theta,
-    so dP_n^m(cos theta)/dtheta = -((n + m) P_{n-1}^m - n x P_n^m) / sin theta.
-    Points on the polar axis (sin theta = 0) or at the centre are refused."""
+    The gradient of a regular wave function is exact in the neighbouring
+    degrees (the addition theorem's differentiation rule; from the Bessel
+    recurrences j_n' -+ (n+1 or -n)/x j_n = j_{n-1} or -j_{n+1} and the
+    recurrences of Y_n^m in cos(theta) and sin(theta) e^{+-i phi}):
+      d/dz R_n^m       = k (A R_{n-1}^m - B R_{n+1}^m)
+      (d/dx + i d/dy) R_n^m = k (C R_{n-1}^{m+1} + D R_{n+1}^{m+1})
+      (d/dx - i d/dy) R_n^m = -k (E R_{n-1}^{m-1} + F R_{n+1}^{m-1})
+    A = sqrt((n^2 - m^2) / ((2n-1)(2n+1))),  B = sqrt(((n+1)^2 - m^2) / ((2n+1)(2n+3))),
+    C = sqrt((n-m)(n-m-1) / ((2n-1)(2n+1))), D = sqrt((n+m+1)(n+m+2) / ((2n+1)(2n+3))),
+    E = sqrt((n+m)(n+m-1) / ((2n-1)(2n+1))), F = sqrt((n-m+1)(n-m+2) / ((2n+1)(2n+3))),
+    with R of order |m| > n taken as zero.  Orthonormal Y with the
+    Condon-Shortley phase (function ylm).  Needs R up to degree p; regular on
+    the polar axis and at the centre."""
     v = np.atleast_2d(np.asarray(v, dtype=np.float64))
-    r, th, ph = cart2sph(v)
-    st, ct = np.sin(th), np.cos(th)
-    if np.any(r <= 0) or np.any(np.abs(st) < 1e-12):
-        raise ValueError("regular_grad_all: point at the centre or on the polar axis")
-    P = p * p
-    ns, ms = nm_of(P)
-    jn = sph_jn(ns[:, None], k * r[None, :])
-    djn = sp.spherical_jn(ns[:, None], k * r[None, :], derivative=True)
-    Y = ylm_all(p, th, ph)
-    dY = np.empty_like(Y)
+    Rall = regular_all(p + 1, k, v)                       # degrees n <= p
+    npts = v.shape[0]
+    zero = np.zeros(npts, dtype=np.complex128)
+
+    def R(n, m):
+        return Rall[idx(n, m)] if 0 <= n and abs(m) <= n else zero
+
+    out = np.zeros((3, p * p, npts), dtype=np.complex128)
     for n in range(p):
+        lo = (2 * n - 1) * (2 * n + 1)
+        hi = (2 * n + 1) * (2 * n + 3)
         for m in range(-n, n + 1):
-            am = abs(m)
-            norm = sqrt((2 * n + 1) / (4 * pi) * factorial(n - am) / factorial(n + am))
-            pn = sp.lpmv(am, n, ct)
-            pn1 = sp.lpmv(am, n - 1, ct) if n >= 1 and am <= n - 1 else 0.0 * ct
-            dp = -((n + am) * pn1 - n * ct * pn) / st
-            d = norm * dp * np.exp(1j * am * ph)
-            if m < 0:
-                d = (-1) ** am * np.conj(d)
-            dY[idx(n, m)] = d
-    dR_drho = k * djn * Y
-    dR_dth = jn * dY / r[None, :]
-    dR_dph = jn * (1j * ms[:, None]) * Y / (r * st)[None, :]
-    e_r = np.stack([st * np.cos(ph), st * np.sin(ph), ct])
-    e_t = np.stack([ct * np.cos(ph), ct * np.sin(ph), -st])
-    e_p = np.stack([-np.sin(ph), np.cos(ph), np.zeros_like(ph)])
-    return (e_r[:, None, :] * dR_drho[None] + e_t[:, None, :] * dR_dth[None]
-            + e_p[:, None, :] * dR_dph[None])
+            A = sqrt((n * n - m * m) / lo) if n > 0 else 0.0
+            B = sqrt(((n + 1) ** 2 - m * m) / hi)
+            C = sqrt((n - m) * (n - m - 1) / lo) if n > 0 else 0.0
+            D = sqrt((n + m + 1) * (n + m + 2) / hi)
+            E = sqrt((n + m) * (n + m - 1) / lo) if n > 0 else 0.0
+            F = sqrt((n - m + 1) * (n - m + 2) / hi)
+            dz = k * (A * R(n - 1, m) - B * R(n + 1, m))
+            dplus = k * (C * R(n - 1, m + 1) + D * R(n + 1, m + 1))
+            dminus = -k * (E * R(n - 1, m - 1) + F * R(n + 1, m - 1))
+            a = idx(n, m)
+            out[0, a] = 0.5 * (dplus + dminus)
+            out[1, a] = (dplus - dminus) / 2j
+            out[2, a] = dz
+    return out

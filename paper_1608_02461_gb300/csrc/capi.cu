@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <new>
 
@@ -37,6 +38,7 @@ struct fmm_tree_ext {
   GmresWork outer;   // A x = b
   BicgWork bicg;     // A x = b by BiCGSTAB
   PrecGraph pg;
+  void* dl_work = nullptr;  // [max(n_vol, n_bnd)] complex128: double-layer sums of the BEM solve with data
 };
 
 // the inner workspaces and boundary vectors of a form
@@ -282,7 +284,11 @@ extern "C" int fmm_apply(fmm_tree* t, int src_set, int tgt_set, const void* d_q_
   if (!t) return HFMM_ERR_INVALID_ARG;
   const int all = HFMM_SET_VOL | HFMM_SET_BND;
   if (src_set <= 0 || (src_set & ~all) || tgt_set <= 0 || (tgt_set & ~all)) return HFMM_ERR_INVALID_ARG;
-  if (mode != HFMM_FWD && mode != HFMM_ADJ && mode != HFMM_DK) return HFMM_ERR_INVALID_ARG;
+  if (mode != HFMM_FWD && mode != HFMM_ADJ && mode != HFMM_DK && mode != HFMM_DLP) return HFMM_ERR_INVALID_ARG;
+  if (mode == HFMM_DLP) {
+    if (src_set != HFMM_SET_BND) return HFMM_ERR_INVALID_ARG;
+    if (!t->lattice || t->n_bnd == 0) return HFMM_ERR_UNSUPPORTED;
+  }
   const int in_set = mode == HFMM_ADJ ? tgt_set : src_set;
   const int out_set = mode == HFMM_ADJ ? src_set : tgt_set;
   if ((in_set & HFMM_SET_VOL) && !d_q_vol) return HFMM_ERR_INVALID_ARG;
@@ -298,12 +304,77 @@ extern "C" int fmm_apply(fmm_tree* t, int src_set, int tgt_set, const void* d_q_
   } else if (mode == HFMM_ADJ) {
     HFMM_TRY(fmm_core_adjoint(t, src_set, tgt_set, s));
     HFMM_TRY(fmm_scatter(t, out_set, (double2*)d_phi_vol, (double2*)d_phi_bnd, s));
+  } else if (mode == HFMM_DLP) {
+    HFMM_TRY(fmm_core_dlp(t, tgt_set, s));
+    HFMM_TRY(fmm_scatter(t, out_set, (double2*)d_phi_vol, (double2*)d_phi_bnd, s));
   } else {
     HFMM_TRY(fmm_core_dk(t, src_set, tgt_set, s));
     HFMM_TRY(fmm_scatter_from(t, t->phis_d, out_set, (double2*)d_phi_vol, (double2*)d_phi_bnd, s));
   }
   HFMM_CUDA_TRY(cudaEventRecord(t->ev1, s));
   return HFMM_OK;
+}
+
+namespace {
+
+// b_i = f_i + (1/h^2) sum of u_Gamma over the boundary neighbours of interior
+// node i (7-point stencil with u = u_Gamma on the boundary nodes; those
+// neighbours are the panel centres).  Node (ix, iy, iz), 1-based, x fastest;
+// panel of face F = 2 axis + side at free coordinates (a, b) (first free
+// coordinate fastest): F n^2 + (b - 1) n + (a - 1).
+__global__ void k_dirichlet_rhs(int n, double inv_h2, const double2* __restrict__ f,
+                                const double2* __restrict__ ub, double2* __restrict__ b) {
+  const int64_t N = (int64_t)n * n * n;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int ix = (int)(i % n) + 1, iy = (int)((i / n) % n) + 1, iz = (int)(i / ((int64_t)n * n)) + 1;
+  const int64_t nn = (int64_t)n * n;
+  double sx = 0.0, sy = 0.0;
+  auto add = [&](int face, int a, int c) {
+    const double2 v = ub[face * nn + (int64_t)(c - 1) * n + (a - 1)];
+    sx += v.x;
+    sy += v.y;
+  };
+  if (ix == 1) add(0, iy, iz);
+  if (ix == n) add(1, iy, iz);
+  if (iy == 1) add(2, ix, iz);
+  if (iy == n) add(3, ix, iz);
+  if (iz == 1) add(4, ix, iy);
+  if (iz == n) add(5, ix, iy);
+  const double2 fi = f[i];
+  b[i] = make_double2(fi.x + inv_h2 * sx, fi.y + inv_h2 * sy);
+}
+
+// g_i = g_i - u_i / 2 - d_i on the boundary (right-hand side of the inner
+// solve with Dirichlet data, written for (-V) q = g)
+template <typename R>
+__global__ void k_bnd_data_rhs(int64_t n, C<R>* __restrict__ g, const double2* __restrict__ u,
+                               const C<R>* __restrict__ dl) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const C<R> gi = g[i], di = dl[i];
+  const double2 ui = u[i];
+  g[i] = mkc<R>(gi.x - R(0.5 * ui.x) - di.x, gi.y - R(0.5 * ui.y) - di.y);
+}
+
+// z_i = z_i - d_i (interior, complex128)
+__global__ void k_sub_inplace(int64_t n, double2* __restrict__ z, const double2* __restrict__ dl) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  z[i] = make_double2(z[i].x - dl[i].x, z[i].y - dl[i].y);
+}
+
+}  // namespace
+
+extern "C" int hfmm_dirichlet_rhs(fmm_tree* t, const void* d_f, const void* d_u_bnd, void* d_b, void* stream) {
+  if (!t || !d_f || !d_u_bnd || !d_b) return HFMM_ERR_INVALID_ARG;
+  if (!t->lattice) return HFMM_ERR_UNSUPPORTED;
+  const int64_t N = (int64_t)t->n * t->n * t->n;
+  const double inv_h2 = 1.0 / (t->h * t->h);
+  k_dirichlet_rhs<<<(unsigned)((N + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      t->n, inv_h2, (const double2*)d_f, (const double2*)d_u_bnd, (double2*)d_b);
+  count_launches(1);
+  return hfmm_last_launch();
 }
 
 // z = M^-1 r (Sec. 5.2-5.3, homogeneous Dirichlet data).  The inner solve
@@ -337,6 +408,60 @@ static int precond_impl_t(fmm_tree* t, const double2* r, double2* z, double inne
   HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, r, h3, q, h2, s));
   HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, s));
   HFMM_TRY(fmm_scatter(t, HFMM_SET_VOL, z, (C<R>*)nullptr, s));
+  if (fmm_device_error(s, true)) return HFMM_ERR_TIMEOUT;
+  return HFMM_OK;
+}
+
+// u = BEM solution with volume data f and Dirichlet data u_Gamma (Sec. 5.2-5.3,
+// Eq. (ubound) then Eq. (uinter)); the preconditioner's passes plus the
+// double layer D (weights h^2 u_Gamma) and the jump u_Gamma / 2:
+//   g = G_{Gamma,Omega} (h^3 f) - u_Gamma / 2 - D_{Gamma,Gamma} u_Gamma
+//   solve (-V) q = g                                   (inner GMRES, Pass B)
+//   u = G_{Omega,Omega} (h^3 f) + G_{Omega,Gamma} (h^2 q) + s_Omega f - D_{Omega,Gamma} u_Gamma
+template <typename R>
+static int bem_dirichlet_impl_t(fmm_tree* t, const double2* f, const double2* ub, double2* u, double inner_rtol,
+                                int inner_maxit, int inner_m, int* inner_iters, cudaStream_t s) {
+  const double h = t->h, h2 = h * h, h3 = h2 * h;
+  fmm_tree_ext* e = ext_of(t);
+  GmresWorkT<R>& W = inner_ws(e, R(0), false);
+  C<R>* g = bnd_g(t, R(0));
+  C<R>* q = bnd_q(t, R(0));
+  if (!e->dl_work) HFMM_TRY(tree_alloc(t, &e->dl_work, sizeof(double2) * (size_t)std::max(t->n_vol, t->n_bnd)));
+  const double2* none = nullptr;
+  const unsigned gb = (unsigned)((t->n_bnd + 255) / 256), gv = (unsigned)((t->n_vol + 255) / 256);
+  // g = N_{Gamma,Omega} f - u / 2 - D_{Gamma,Gamma} u
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL, f, h3, none, 0.0, s));
+  HFMM_TRY(fmm_core(t, HFMM_SET_VOL, HFMM_SET_BND, s));
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, g, s));
+  C<R>* dl_b = reinterpret_cast<C<R>*>(e->dl_work);
+  HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, ub, h2, s));
+  HFMM_TRY(fmm_core_dlp(t, HFMM_SET_BND, s));
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, dl_b, s));
+  k_bnd_data_rhs<R><<<gb, 256, 0, s>>>(t->n_bnd, g, ub, dl_b);
+  count_launches(1);
+  HFMM_TRY(hfmm_last_launch());
+  // (-V) q = g
+  HFMM_TRY(gmres_work_reserve(W, t->n_bnd, inner_m, false));
+  DevOpT<R> negV = [t, h2, s](const C<R>* in, C<R>* out) -> int {
+    HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, in, -h2, s));
+    HFMM_TRY(fmm_core(t, HFMM_SET_BND, HFMM_SET_BND, s));
+    return fmm_scatter(t, HFMM_SET_BND, nullptr, out, s);
+  };
+  HFMM_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(C<R>) * t->n_bnd, s));
+  GmresResult ir;
+  HFMM_TRY(gmres_run<R>(W, negV, nullptr, g, q, inner_m, inner_rtol, inner_maxit, true, false, &ir, nullptr, 0, s));
+  if (inner_iters) *inner_iters = ir.iters;
+  // u = N_{Omega,Omega} f + V_{Omega,Gamma} q + s_Omega f - D_{Omega,Gamma} u_Gamma
+  HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, f, h3, q, h2, s));
+  HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, s));
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_VOL, u, (C<R>*)nullptr, s));
+  double2* dl_v = reinterpret_cast<double2*>(e->dl_work);
+  HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, ub, h2, s));
+  HFMM_TRY(fmm_core_dlp(t, HFMM_SET_VOL, s));
+  HFMM_TRY(fmm_scatter(t, HFMM_SET_VOL, dl_v, (double2*)nullptr, s));
+  k_sub_inplace<<<gv, 256, 0, s>>>(t->n_vol, u, dl_v);
+  count_launches(1);
+  HFMM_TRY(hfmm_last_launch());
   if (fmm_device_error(s, true)) return HFMM_ERR_TIMEOUT;
   return HFMM_OK;
 }
@@ -455,6 +580,23 @@ extern "C" int fmm_precond_apply(fmm_tree* t, const void* d_r, void* d_z, double
   HFMM_CUDA_TRY(cudaEventRecord(t->ev0, s));
   HFMM_TRY(precond_impl(t, (const double2*)d_r, (double2*)d_z, inner_rtol, inner_maxit, inner_m,
                         inner_iters, s));
+  HFMM_CUDA_TRY(cudaEventRecord(t->ev1, s));
+  return HFMM_OK;
+}
+
+extern "C" int bem_solve_dirichlet(fmm_tree* t, const void* d_f, const void* d_u_bnd, void* d_u, double inner_rtol,
+                                   int inner_maxit, int inner_m, int* inner_iters, void* stream) {
+  if (!t || !d_f || !d_u_bnd || !d_u) return HFMM_ERR_INVALID_ARG;
+  if (!t->lattice || t->n_bnd == 0) return HFMM_ERR_UNSUPPORTED;
+  if (!(inner_rtol > 0.0) || inner_maxit < 1 || inner_m < 1 || inner_m > 500) return HFMM_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  HFMM_CUDA_TRY(cudaEventRecord(t->ev0, s));
+  if (t->precision == HFMM_FP32)
+    HFMM_TRY(bem_dirichlet_impl_t<float>(t, (const double2*)d_f, (const double2*)d_u_bnd, (double2*)d_u,
+                                         inner_rtol, inner_maxit, inner_m, inner_iters, s));
+  else
+    HFMM_TRY(bem_dirichlet_impl_t<double>(t, (const double2*)d_f, (const double2*)d_u_bnd, (double2*)d_u,
+                                          inner_rtol, inner_maxit, inner_m, inner_iters, s));
   HFMM_CUDA_TRY(cudaEventRecord(t->ev1, s));
   return HFMM_OK;
 }

@@ -42,7 +42,18 @@ struct FmmDev {
   T k;
   const int* skip;  // when set and nonzero, every kernel of the pass returns at once
   C<T>* near;       // when set: P2P writes its sums here (=) and L2P adds them
+  // lattice trees: sorted position -> original id, for the face (and outward
+  // normal) of a boundary panel: face = (orig - n_vol) / nn, nn = n^2, faces
+  // x=0, x=1, y=0, y=1, z=0, z=1 with normals -e_x, +e_x, -e_y, ...
+  const int64_t* orig;
+  int64_t n_vol, nn;
 };
+
+// face of the boundary panel at sorted position j (lattice trees)
+template <typename T>
+__device__ __forceinline__ int panel_face(const FmmDev<T>& d, int j) {
+  return (int)((d.orig[j] - d.n_vol) / d.nn);
+}
 
 // P2P result of target i: into the near-field buffer, or added to phis
 template <typename T>
@@ -154,10 +165,78 @@ __device__ void regular_basis_dk_conj(int p, T k, T dx, T dy, T dz, C<T> q, C<T>
   }
 }
 
+// conj(n . grad R_a)(v) * q for all a < P: the multipole row of a dipole of
+// strength q with the outward normal n of boundary face `face` (n = -e_x for
+// x=0, +e_x for x=1, ...), Sec. 5.2 (normal derivative in the double-layer
+// term of Eq. (bem)).  With d+- = d/dx +- i d/dy the gradient of R_l^m =
+// j_l Y_l^m (orthonormal Y, Condon-Shortley phase) is exact in the degrees
+// l -+ 1:
+//   d/dz R_l^m = k (A R_{l-1}^m - B R_{l+1}^m)
+//   d+   R_l^m = k (C R_{l-1}^{m+1} + D R_{l+1}^{m+1})
+//   d-   R_l^m = -k (E R_{l-1}^{m-1} + F R_{l+1}^{m-1})
+//   A = sqrt((l^2 - m^2) / ((2l-1)(2l+1))),   B = sqrt(((l+1)^2 - m^2) / ((2l+1)(2l+3))),
+//   C = sqrt((l-m)(l-m-1) / ((2l-1)(2l+1))),  D = sqrt((l+m+1)(l+m+2) / ((2l+1)(2l+3))),
+//   E = sqrt((l+m)(l+m-1) / ((2l-1)(2l+1))),  F = sqrt((l-m+1)(l-m+2) / ((2l+1)(2l+3))),
+// terms of order |m'| > l' being zero; so R is needed up to degree p, and no
+// division by sin(theta) occurs (points on the polar axis are regular).
+template <typename T>
+__device__ void regular_basis_dn_conj(int p, T k, T dx, T dy, T dz, int face, C<T> q, C<T>* out) {
+  T r, ct, st, cp, sp;
+  direction<T>(dx, dy, dz, r, ct, st, cp, sp);
+  T jn[HFMM_MAX_P + 1];
+  T pl[(HFMM_MAX_P + 1) * (HFMM_MAX_P + 2) / 2];
+  C<T> em[HFMM_MAX_P + 1];  // e^{i m phi}, m <= p
+  sph_bessel_j<T>(k * r, p + 1, jn);
+  legendre_bar<T>(ct, st, p + 1, pl);
+  em[0] = mkc<T>(1, 0);
+  for (int m = 1; m <= p; ++m) em[m] = mkc<T>(em[m - 1].x * cp - em[m - 1].y * sp, em[m - 1].x * sp + em[m - 1].y * cp);
+  // R_n^m for 0 <= n <= p, zero outside |m| <= n
+  auto Rnm = [&](int n, int m) -> C<T> {
+    const int am = m < 0 ? -m : m;
+    if (n < 0 || am > n) return mkc<T>(0, 0);
+    const T v = jn[n] * pl[n * (n + 1) / 2 + am];
+    C<T> R = mkc<T>(v * em[am].x, v * em[am].y);
+    if (m < 0) {  // R_n^{-m} = (-1)^m conj(R_n^m)
+      R = conjc<T>(R);
+      if (am & 1) R = mkc<T>(-R.x, -R.y);
+    }
+    return R;
+  };
+  const int axis = face >> 1;
+  const T sgn = (face & 1) ? T(1) : T(-1);
+  for (int l = 0; l < p; ++l) {
+    const T den_lo = T((2 * l - 1) * (2 * l + 1)), den_hi = T((2 * l + 1) * (2 * l + 3));
+    for (int m = -l; m <= l; ++m) {
+      C<T> g;  // d/d(axis) R_l^m
+      if (axis == 2) {
+        const T A = l > 0 ? sqrt(T(l * l - m * m) / den_lo) : T(0);
+        const T B = sqrt(T((l + 1) * (l + 1) - m * m) / den_hi);
+        const C<T> lo = Rnm(l - 1, m), hi = Rnm(l + 1, m);
+        g = mkc<T>(k * (A * lo.x - B * hi.x), k * (A * lo.y - B * hi.y));
+      } else {
+        const T Cc = l > 0 ? sqrt(T((l - m) * (l - m - 1)) / den_lo) : T(0);
+        const T Dd = sqrt(T((l + m + 1) * (l + m + 2)) / den_hi);
+        const T Ee = l > 0 ? sqrt(T((l + m) * (l + m - 1)) / den_lo) : T(0);
+        const T Ff = sqrt(T((l - m + 1) * (l - m + 2)) / den_hi);
+        const C<T> a1 = Rnm(l - 1, m + 1), a2 = Rnm(l + 1, m + 1);
+        const C<T> b1 = Rnm(l - 1, m - 1), b2 = Rnm(l + 1, m - 1);
+        const C<T> dp = mkc<T>(k * (Cc * a1.x + Dd * a2.x), k * (Cc * a1.y + Dd * a2.y));
+        const C<T> dm = mkc<T>(-k * (Ee * b1.x + Ff * b2.x), -k * (Ee * b1.y + Ff * b2.y));
+        if (axis == 0)  // d/dx = (d+ + d-) / 2
+          g = mkc<T>(T(0.5) * (dp.x + dm.x), T(0.5) * (dp.y + dm.y));
+        else            // d/dy = (d+ - d-) / (2 i)
+          g = mkc<T>(T(0.5) * (dp.y - dm.y), -T(0.5) * (dp.x - dm.x));
+      }
+      out[l * l + l + m] = cmul<T>(conjc<T>(mkc<T>(sgn * g.x, sgn * g.y)), q);
+    }
+  }
+}
+
 // one block per leaf; CHUNK points' basis rows staged in shared memory, then
 // summed per coefficient.  Output Mout (leaf level), weights times `fac`;
-// DK: derivative of the basis with respect to k.
-template <typename T, bool DK>
+// BASIS 0: R_a; 1: derivative of the basis with respect to k; 2: normal
+// derivative at boundary panels (dipole sources).
+template <typename T, int BASIS>
 __global__ void k_p2m(FmmDev<T> d, C<T>* Mout, int64_t leaf_off, int src_set, int chunk, C<T> fac,
                       const int* __restrict__ list) {
   HFMM_SKIP_IF(d);
@@ -182,8 +261,10 @@ __global__ void k_p2m(FmmDev<T> d, C<T>* Mout, int64_t leaf_off, int src_set, in
         T dx, dy, dz;
         local_coords<T>(d, j, leaf, dx, dy, dz);
         C<T> q = cmul<T>(d.qs[j], fac);
-        if constexpr (DK)
+        if constexpr (BASIS == 1)
           regular_basis_dk_conj<T>(d.p, d.k, dx, dy, dz, q, row);
+        else if constexpr (BASIS == 2)
+          regular_basis_dn_conj<T>(d.p, d.k, dx, dy, dz, panel_face<T>(d, j), q, row);
         else
           regular_basis<T, true>(d.p, d.k, dx, dy, dz, q, row);
       } else {
@@ -1618,7 +1699,11 @@ __device__ __forceinline__ T rsqrt_t(T x) {
   else return rsqrtf(x);
 }
 
-// KMODE 0: G = e^{ikr}/(4 pi r); 1: conj(G) (adjoint); 2: dG/dk = i e^{ikr}/(4 pi) (tangent)
+// KMODE 0: G = e^{ikr}/(4 pi r); 1: conj(G) (adjoint); 2: dG/dk = i e^{ikr}/(4 pi) (tangent);
+// 3: dG/dn_y = (i k r - 1) e^{ikr} / (4 pi r^2) (y - x).n_y / r, boundary
+// sources of a lattice tree (double layer; the staged record's fourth word
+// carries the source's normal as +-(axis + 1)); no self term (the own flat
+// panel contributes nothing)
 template <typename T, int W, int KMODE>
 __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restrict__ near_off,
                                                 int near_count, int src_set, int tgt_set,
@@ -1719,6 +1804,10 @@ __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restri
         sp.y = ly + nb_sh[lo][1];
         sp.z = lz + nb_sh[lo][2];
         sp.pad = T(0);
+        if constexpr (KMODE == 3) {
+          const int f = panel_face<T>(d, j);
+          sp.pad = T((f & 1) ? (f >> 1) + 1 : -((f >> 1) + 1));
+        }
         spos[e] = sp;
         sq[e] = cscale<T>(d.qs[j], inv4pi);
       }
@@ -1744,9 +1833,18 @@ __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restri
             const T wr = q.x * rinv, wi = q.y * rinv;
             part.x = fma(cs, wr, fma(sn, wi, part.x));
             part.y = fma(cs, wi, fma(-sn, wr, part.y));
-          } else {  // i e^{ikr} q (zero-distance pairs masked through rinv)
+          } else if constexpr (KMODE == 2) {  // i e^{ikr} q (zero-distance pairs masked through rinv)
             const T m = rinv > T(0) ? T(1) : T(0);
             const T gr = -sn * m, gi = cs * m;
+            part.x = fma(gr, q.x, fma(-gi, q.y, part.x));
+            part.y = fma(gr, q.y, fma(gi, q.x, part.y));
+          } else {  // (i k r - 1) e^{ikr} (y - x).n / r^3 q; y - x = -(dx, dy, dz)
+            const int code = (int)sp.pad;
+            const int ax = (code < 0 ? -code : code) - 1;
+            const T dn = ax == 0 ? dx : (ax == 1 ? dy : dz);
+            const T g = (code > 0 ? -dn : dn) * rinv * rinv * rinv;  // zero at zero distance
+            const T kr = k * r;
+            const T gr = g * (-cs - kr * sn), gi = g * (kr * cs - sn);
             part.x = fma(gr, q.x, fma(-gi, q.y, part.x));
             part.y = fma(gr, q.y, fma(gi, q.x, part.y));
           }
@@ -1770,7 +1868,7 @@ __global__ void __launch_bounds__(256) k_p2p_v2(FmmDev<T> d, const int* __restri
     }
     if (active && sub == 0) {
       const bool is_vol = i < d.leaf_mid[leaf];
-      if ((is_vol && (src_set & HFMM_SET_VOL)) || (!is_vol && (src_set & HFMM_SET_BND))) {
+      if (KMODE != 3 && ((is_vol && (src_set & HFMM_SET_VOL)) || (!is_vol && (src_set & HFMM_SET_BND)))) {
         double2 sg = is_vol ? sig_vol : sig_bnd;
         cfma<T>(tot, mkc<T>(T(sg.x), T(sg.y)), d.qs[i]);
       }
@@ -2058,6 +2156,9 @@ FmmDev<T> make_dev(fmm_tree* t) {
   d.k = T(t->k);
   d.skip = t->skip;
   d.near = nullptr;
+  d.orig = t->orig;
+  d.n_vol = t->n_vol;
+  d.nn = (int64_t)t->n * t->n;
   return d;
 }
 
@@ -2162,8 +2263,23 @@ int launch_p2m(fmm_tree* t, const FmmDev<T>& d, C<T>* Mout, int src_set, C<T> fa
   }
   const int chunk = 32;
   const size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
-  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, false>, sm_p2m));
-  k_p2m<T, false><<<na, 64, sm_p2m, s>>>(d, Mout, t->level_off[L], src_set, chunk, fac, act_list(t, src_set, L));
+  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, 0>, sm_p2m));
+  k_p2m<T, 0><<<na, 64, sm_p2m, s>>>(d, Mout, t->level_off[L], src_set, chunk, fac, act_list(t, src_set, L));
+  return hfmm_last_launch();
+}
+
+// dipole P2M over the boundary panels (double layer): generic kernel, the
+// basis rows being normal derivatives
+template <typename T>
+int launch_p2m_dipole(fmm_tree* t, const FmmDev<T>& d, C<T>* Mout, cudaStream_t s) {
+  const int L = t->L, P = t->P;
+  const int na = act_n(t, HFMM_SET_BND, L);
+  if (!na) return HFMM_OK;
+  const int chunk = 32;
+  const size_t sm_p2m = (size_t)chunk * P * sizeof(C<T>);
+  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, 2>, sm_p2m));
+  k_p2m<T, 2><<<na, 64, sm_p2m, s>>>(d, Mout, t->level_off[L], HFMM_SET_BND, chunk, mkc<T>(1, 0),
+                                     act_list(t, HFMM_SET_BND, L));
   return hfmm_last_launch();
 }
 
@@ -2213,7 +2329,7 @@ template <typename T, int KMODE>
 int p2p_stage(fmm_tree* t, const FmmDev<T>& d, int src_set, int tgt_set, double2 sv, double2 sb,
               cudaStream_t s) {
   const int nleaf = 1 << (3 * t->L);
-  if constexpr (KMODE != 2) {
+  if constexpr (KMODE == 0 || KMODE == 1) {
     if (t->lat_D > 0 && t->use_lattice_p2p && t->near_count <= 128 &&
         (sizeof(T) == 4 || t->lat_tab64_fits))
       return launch_p2p_lat<T, KMODE>(t, d, src_set, tgt_set, sv, sb, s);
@@ -2317,10 +2433,10 @@ int core_dk_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   C<T>* phd = reinterpret_cast<C<T>*>(t->phis_d);
   const int chunk = 32;
   size_t sm_p2m = (size_t)chunk * P * csz;
-  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, true>, sm_p2m));
+  HFMM_TRY(set_smem<T>((const void*)k_p2m<T, 1>, sm_p2m));
   HFMM_TRY(launch_p2m<T>(t, d, d.M, src_set, mkc<T>(1, 0), s));
   if (act_n(t, src_set, L))
-    k_p2m<T, true><<<act_n(t, src_set, L), 64, sm_p2m, s>>>(d, Md, t->level_off[L], src_set, chunk, mkc<T>(1, 0), act_list(t, src_set, L));
+    k_p2m<T, 1><<<act_n(t, src_set, L), 64, sm_p2m, s>>>(d, Md, t->level_off[L], src_set, chunk, mkc<T>(1, 0), act_list(t, src_set, L));
   size_t sm8 = 8 * (size_t)P * csz;
   HFMM_TRY(set_smem<T>((const void*)k_m2m<T>, sm8));
   for (int l = L - 1; l >= 2; --l) {
@@ -2367,8 +2483,10 @@ int core_dk_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   return hfmm_last_launch();
 }
 
+// dipole: double-layer pass (boundary sources with their outward normals,
+// dipole P2M and P2P, no self term); otherwise the single-layer pass
 template <typename T>
-int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
+int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s, bool dipole = false) {
   FmmDev<T> d = make_dev<T>(t);
   const int P = t->P, L = t->L;
   const int nleaf = 1 << (3 * L);
@@ -2384,7 +2502,8 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   // the targets are the boundary points: there the far-field kernels are
   // small and latency-bound and leave most SMs idle (with volume targets both
   // chains are compute-bound and running them together is slower)
-  const bool overlap = t->overlap_near && t->near_stream && t->phis_near && !(tgt_set & HFMM_SET_VOL);
+  const bool overlap =
+      !dipole && t->overlap_near && t->near_stream && t->phis_near && !(tgt_set & HFMM_SET_VOL);
   if (overlap) {
     d.near = reinterpret_cast<C<T>*>(t->phis_near);
     cudaStream_t sn = t->near_stream;
@@ -2397,7 +2516,10 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   }
   // P2M
   tm.begin(HFMM_STAGE_P2M, s);
-  HFMM_TRY(launch_p2m<T>(t, d, d.M, src_set, mkc<T>(1, 0), s));
+  if (dipole)
+    HFMM_TRY(launch_p2m_dipole<T>(t, d, d.M, s));
+  else
+    HFMM_TRY(launch_p2m<T>(t, d, d.M, src_set, mkc<T>(1, 0), s));
   tm.end(1, s);
   count_launches(1);
   // M2M, levels L-1 .. 2
@@ -2436,7 +2558,10 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   tm.end(1, s);
   if (!overlap) {
     tm.begin(HFMM_STAGE_P2P, s);
-    HFMM_TRY(p2p_stage<T, 0>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));
+    if (dipole)
+      HFMM_TRY(p2p_stage<T, 3>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));
+    else
+      HFMM_TRY(p2p_stage<T, 0>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));
     tm.end(1, s, tm.on ? p2p_work(t, src_set, tgt_set) : 0.0);
   }
   count_launches(2);
@@ -2541,6 +2666,12 @@ int set_smem_any(const void* fn, size_t bytes) { return set_smem<float>(fn, byte
 int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   if (t->precision == HFMM_FP32) return core_impl<float>(t, src_set, tgt_set, s);
   return core_impl<double>(t, src_set, tgt_set, s);
+}
+
+int fmm_core_dlp(fmm_tree* t, int tgt_set, cudaStream_t s) {
+  if (!t->lattice || !t->orig) return HFMM_ERR_UNSUPPORTED;
+  if (t->precision == HFMM_FP32) return core_impl<float>(t, HFMM_SET_BND, tgt_set, s, true);
+  return core_impl<double>(t, HFMM_SET_BND, tgt_set, s, true);
 }
 
 int fmm_core_adjoint(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {

@@ -322,6 +322,9 @@ int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol,
 int fmm_gather(fmm_tree* t, int src_set, const double2* q_vol, double scale_vol,
                const float2* q_bnd, double scale_bnd, cudaStream_t s);
 int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
+// double-layer pass (lattice trees): dipole strengths in qs on the boundary
+// panels, phis_i = sum_{j != i} q_j dG/dn_y(x_i, y_j) on tgt_set
+int fmm_core_dlp(fmm_tree* t, int tgt_set, cudaStream_t s);
 // adjoint pass: weights in qs on the points of tgt_set, result in phis on src_set
 int fmm_core_adjoint(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
 // tangent pass: d(phi)/dk into phis for the weights in qs

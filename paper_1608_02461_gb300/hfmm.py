@@ -27,6 +27,7 @@ SET_BND = 2
 FWD = 0
 ADJ = 1
 DK = 2
+DLP = 3
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhfmm.so")
 
@@ -78,6 +79,11 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "hfmm_fdm_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
+    "bem_solve_dirichlet": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "hfmm_dirichlet_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "gmres_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.POINTER(hfmm_gmres_params),
                                    ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
@@ -200,7 +206,8 @@ class Tree:
     def apply(self, q_vol=None, q_bnd=None, src=SET_VOL | SET_BND, tgt=SET_VOL | SET_BND,
               phi_vol=None, phi_bnd=None, mode=FWD, stream=None):
         """fmm_apply.  FWD/DK: q on `src`, phi on `tgt`; ADJ: q on `tgt`,
-        phi on `src` (conjugate transpose)."""
+        phi on `src` (conjugate transpose); DLP: double layer, q on the
+        boundary panels (src = SET_BND), phi on `tgt`."""
         torch = _torch()
         dev = (q_vol if q_vol is not None else q_bnd).device
         out_set = src if mode == ADJ else tgt
@@ -227,6 +234,33 @@ class Tree:
                                      ctypes.byref(its), _stream_ptr(stream))
         _check(st, "fmm_precond_apply")
         return z, its.value
+
+    def dirichlet_rhs(self, f, u_bnd, b=None, stream=None):
+        """hfmm_dirichlet_rhs: b = f + (1/h^2) (Dirichlet values at the
+        boundary neighbours of each interior node)."""
+        torch = _torch()
+        _dev_c128(f, self.n_vol, "f")
+        _dev_c128(u_bnd, self.n_bnd, "u_bnd")
+        if b is None:
+            b = torch.empty_like(f)
+        _check(lib().hfmm_dirichlet_rhs(self._h, _ptr(f), _ptr(u_bnd), _ptr(b), _stream_ptr(stream)),
+               "hfmm_dirichlet_rhs")
+        return b
+
+    def bem_solve_dirichlet(self, f, u_bnd, u=None, inner_rtol=1e-4, inner_maxit=200, inner_m=50,
+                            stream=None):
+        """bem_solve_dirichlet: the BEM solution with volume data f and
+        Dirichlet data u_bnd.  Returns (u, inner iterations)."""
+        torch = _torch()
+        _dev_c128(f, self.n_vol, "f")
+        _dev_c128(u_bnd, self.n_bnd, "u_bnd")
+        if u is None:
+            u = torch.empty_like(f)
+        its = ctypes.c_int(0)
+        st = lib().bem_solve_dirichlet(self._h, _ptr(f), _ptr(u_bnd), _ptr(u), inner_rtol, inner_maxit,
+                                       inner_m, ctypes.byref(its), _stream_ptr(stream))
+        _check(st, "bem_solve_dirichlet")
+        return u, its.value
 
     def fdm(self, u, out=None, stream=None):
         torch = _torch()

@@ -39,9 +39,26 @@ def test_regular_gradient_degree_zero_closed_form():
     assert np.abs(got - want).max() < 1e-14
 
 
-def test_regular_gradient_refuses_the_polar_axis():
-    with pytest.raises(ValueError):
-        S.regular_grad_all(3, 1.0, np.array([[0.0, 0.0, 0.2]]))
+def test_regular_gradient_on_the_polar_axis_and_at_the_centre():
+    """Points on the z axis (either side) and the centre itself, where
+    spherical coordinates are singular: central differences of R_a still
+    agree (lattice panels do lie on the axis of their leaf centre when n + 1
+    is a power of two)."""
+    v = np.array([[0.0, 0.0, 0.2], [0.0, 0.0, -0.35], [0.0, 0.0, 0.0], [1e-9, 0.0, 0.3]])
+    p, k = 6, 5.0
+    g = S.regular_grad_all(p, k, v)
+    # five-point differences with a wide step: near the axis the Legendre
+    # values of R carry the cancellation of 1 - cos^2(theta), so the step
+    # stays far from the axis scale of rounding
+    d = 1e-3
+
+    def Rv(x):
+        return S.regular_all(p, k, x)
+
+    fd = np.stack([(-Rv(v + 2 * d * e) + 8 * Rv(v + d * e) - 8 * Rv(v - d * e) + Rv(v - 2 * d * e)) / (12 * d)
+                   for e in np.eye(3)])
+    assert np.all(np.isfinite(g))
+    assert np.abs(g - fd).max() < 1e-8 * max(1.0, np.abs(g).max())
 
 
 def test_dgreen_dn_is_the_source_normal_derivative_of_g():
