@@ -19,6 +19,7 @@ Modules
   translations M2M / M2L / L2L operators (exact re-expansion, then truncation)
   fmm          P2M, M2M, M2L, L2L, L2P, P2P, self terms, direct sum
   bem          the BEM-coupled FMM preconditioner (Passes A, B, C)
+  tangent      exact d/dk of the truncated FMM (every stage by the product rule)
   dirichlet    inhomogeneous Dirichlet data: double-layer kernel and sums
                (direct and dipole FMM), the FDM lift, the BEM solve with data
   fdm          the 7-point finite-difference Helmholtz operator
