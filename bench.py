@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-solve batched measurement")
     ap.add_argument("--no-bicgstab", action="store_true", help="skip the BiCGSTAB solve of the same system")
+    ap.add_argument("--dirichlet", action="store_true",
+                    help="also time the solve with Dirichlet data (plane-wave boundary values): "
+                         "the FDM system with the boundary lift, from zero and from the BEM "
+                         "solution with the data, and the double-layer FMM apply")
     ap.add_argument("--batched-maxit", type=int, default=200)
     ap.add_argument("--sweep", choices=("kh", "p"),
                     help="print one JSON line per point of a sweep (fixed kh = 0.3125 over n, or the "
@@ -427,6 +431,49 @@ def run_ours(args, world, rank, local):
                 "gmres_same_inner": {"time_to_solution_s": e0.elapsed_time(e1) * 1e-3, "iters": ig.iters,
                                      "inner_iters_total": ig.inner_iters_total, "relres_true": ig.relres_true}}
 
+    # inhomogeneous Dirichlet data: u = plane wave on the boundary, volume data
+    # b; A u = b + lift(u_Gamma) solved from zero and from the BEM solution
+    # with the data (double layer included), and the double-layer apply alone
+    dirich = None
+    if args.dirichlet:
+        ub = torch.from_numpy(inputs.plane_wave_boundary(n, w["k"])).to(dev)
+        ikw = dict(inner_rtol=args.inner_rtol, inner_maxit=args.inner_maxit, inner_m=args.inner_maxit)
+        bd = tree.dirichlet_rhs(b, ub)
+        tree.gmres(bd, **gm)                                   # warm-up
+        x0, _ = tree.bem_solve_dirichlet(b, ub, **ikw)
+        flush.fill_(1.0)
+        e0.record(stream)
+        tree.dirichlet_rhs(b, ub, b=bd)
+        _, iz = tree.gmres(bd, **gm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_zero = e0.elapsed_time(e1) * 1e-3
+        flush.fill_(1.0)
+        e0.record(stream)
+        tree.dirichlet_rhs(b, ub, b=bd)
+        _, its_bem = tree.bem_solve_dirichlet(b, ub, u=x0, **ikw)
+        _, ibm = tree.gmres(bd, x=x0, **gm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_bem = e0.elapsed_time(e1) * 1e-3
+        tgt_all = hfmm.SET_VOL | hfmm.SET_BND
+        pv_d, pb_d = tree.apply(None, ub, src=hfmm.SET_BND, tgt=tgt_all, mode=hfmm.DLP)
+        e0.record(stream)
+        for _ in range(5):
+            tree.apply(None, ub, src=hfmm.SET_BND, tgt=tgt_all, phi_vol=pv_d, phi_bnd=pb_d, mode=hfmm.DLP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dl_ms = e0.elapsed_time(e1) / 5
+        dirich = {"boundary_data": "plane wave exp(i k d.x), d = (1, 2, 2)/3",
+                  "from_zero": {"time_to_solution_s": t_zero, "gmres_iters": iz.iters,
+                                "inner_iters_total": iz.inner_iters_total, "relres_true": iz.relres_true,
+                                "converged": iz.status == 0},
+                  "from_bem_solution": {"time_to_solution_s": t_bem, "gmres_iters": ibm.iters,
+                                        "inner_iters_total": ibm.inner_iters_total + its_bem,
+                                        "relres_true": ibm.relres_true, "converged": ibm.status == 0},
+                  "double_layer_apply_ms": dl_ms,
+                  "double_layer_apply_mpts_s": (n ** 3 + 6 * n * n) / (dl_ms * 1e-3) / 1e6}
+
     # batched form: 48 independent solves of uneven size and wavenumber
     batched = None
     if not args.no_batched:
@@ -495,6 +542,8 @@ def run_ours(args, world, rank, local):
                     "d2h_bytes_per_step": nbytes},
             "fp64": fp64, "bicgstab": bicg, "batched": batched, "cpu_baseline": cpu, "clocks": clk,
         }
+        if dirich is not None:
+            line["dirichlet"] = dirich
         print(json.dumps(line), flush=True)
     tree.close()
     if world > 1:

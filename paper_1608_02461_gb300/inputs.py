@@ -86,6 +86,33 @@ def rhs(kind: str, n: int, seed: int) -> np.ndarray:
     raise ValueError(f"unknown rhs kind {kind!r}")
 
 
+def boundary_coords(n: int) -> np.ndarray:
+    """Centres of the 6 n^2 boundary panels (boundary grid nodes off the
+    cube's edges), faces x=0, x=1, y=0, y=1, z=0, z=1, first free coordinate
+    fastest within a face: shape (6 n^2, 3)."""
+    h = 1.0 / (n + 1)
+    a = np.arange(1, n + 1) * h
+    B, A = np.meshgrid(a, a, indexing="ij")          # A (first free) fastest
+    out = []
+    for axis in range(3):
+        free = [c for c in range(3) if c != axis]
+        for val in (0.0, 1.0):
+            x = np.zeros((n * n, 3))
+            x[:, axis] = val
+            x[:, free[0]] = A.ravel()
+            x[:, free[1]] = B.ravel()
+            out.append(x)
+    return np.concatenate(out)
+
+
+def plane_wave_boundary(n: int, k: float, direction=(1.0, 2.0, 2.0)) -> np.ndarray:
+    """Dirichlet data u_Gamma = exp(i k d.x) at the panel centres, d the unit
+    vector along `direction` (synthetic boundary data), complex128 (6 n^2,)."""
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    return np.exp(1j * k * boundary_coords(n) @ d)
+
+
 def workload_rhs(name: str) -> np.ndarray:
     w = WORKLOADS[name]
     return rhs(w["rhs"], w["n"], w["seed"])

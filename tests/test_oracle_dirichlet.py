@@ -11,6 +11,7 @@ from oracle import dirichlet as D
 from oracle import fdm, geometry, gmres
 from oracle import fmm as F
 from oracle import special as S
+from paper_1608_02461_gb300 import inputs
 
 
 def test_regular_gradient_matches_finite_differences():
@@ -283,3 +284,14 @@ def test_fdm_solve_with_dirichlet_data():
     assert info["converged"] and info1["converged"]
     assert np.linalg.norm(x1 - x) / np.linalg.norm(x) < 1e-8
     assert info1["iters"] <= info["iters"]
+
+
+def test_input_boundary_data_follows_the_panel_order():
+    """The seeded-input module's panel centres and plane-wave data are in the
+    oracle's panel order (faces x=0, x=1, y=0, y=1, z=0, z=1, first free
+    coordinate fastest)."""
+    for n in (3, 6):
+        X, _ = geometry.boundary_panels(n)
+        assert np.array_equal(inputs.boundary_coords(n), X)
+        d = np.array([1.0, 2.0, 2.0]) / 3.0
+        assert np.allclose(inputs.plane_wave_boundary(n, 4.0), np.exp(4j * X @ d), rtol=0, atol=1e-15)
