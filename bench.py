@@ -352,6 +352,24 @@ def run_ours(args, world, rank, local):
                               "weighted by the solve's pass mix" if traffic is not None else None}
     roof["peak_kind"] = peak_kind if roof["bound"] == "hbm" else "derived"
     stage_summary = {k: {"ms": v[0], "launches": v[1]} for k, v in stages.items()}
+    # the far field's M2L stage over one fully timed solve (outside the timed
+    # region): algorithmic 8 P^2 flop per cell pair over all its launches
+    # (tensor-core kernel at levels >= 4 of the volume-target pass, CUDA-core
+    # pipelines and pair lists elsewhere)
+    m2l_ms, m2l_nl, m2l_flop = stages["m2l"]
+    roof_m2l = None
+    if m2l_ms > 0 and m2l_flop > 0:
+        a2 = m2l_flop / (m2l_ms * 1e-3) / 1e12
+        p2 = FP32_ALU_PEAK_TFLOPS if lattice else FP64_PEAK_TFLOPS
+        roof_m2l = {"bound": "alu", "kernel": "M2L stage (k_m2l_tc, k_m2l_ws, k_m2l_pairs)", "achieved": a2,
+                    "peak": p2, "unit": "TFLOP/s", "frac": a2 / p2, "launches": m2l_nl,
+                    "ms_per_solve": m2l_ms, "work_unit": "8 P^2 flop per cell pair",
+                    "peak_source": ("FP32 FMA pipes: 152 SM x 128 lanes x 2 flop x 2.07 GHz" if lattice
+                                    else "nominal FP64 rate"),
+                    # tensor-core M2L in FP32 accuracy: three TF32 products per
+                    # algorithmic one; TF32 rate = bf16 dense rate x nominal 1.1 / 2.25
+                    "frac_of_tf32_tensor": (a2 / (peaks["bf16_tflops"] * 1.1 / 2.25 / 3)) if lattice else None,
+                    "source": "stage timers of one fully timed solve (outside the timed region)"}
 
     # FMM apply throughput (full apply, all points sources and targets)
     qv = torch.from_numpy(inputs.complex_normal(n ** 3, 51)).to(dev)
@@ -537,7 +555,7 @@ def run_ours(args, world, rank, local):
             "solves_per_s": world / (ms * 1e-3),
             "fmm_apply_ms": app_ms, "fmm_apply_mpts_s": mpts,
             "gpu_launches": int(launches),
-            "roofline": roof, "stages_per_solve": stage_summary,
+            "roofline": roof, "roofline_m2l": roof_m2l, "stages_per_solve": stage_summary,
             "e2e": {"value": e2e_ms * 1e-3, "unit": "s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
             "fp64": fp64, "bicgstab": bicg, "batched": batched, "cpu_baseline": cpu, "clocks": clk,
