@@ -166,6 +166,7 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   if (const char* g = getenv("HFMM_GRAPHS")) t->use_graphs = atoi(g) != 0;
   if (const char* v = getenv("HFMM_M2L_VARIANT")) t->m2l_variant = atoi(v);
   if (const char* v = getenv("HFMM_LATTICE_P2P")) t->use_lattice_p2p = atoi(v) != 0;
+  if (const char* v = getenv("HFMM_P2P_TILE")) t->lat_tile = atoi(v) != 0;
   if (const char* v = getenv("HFMM_BASIS_TABLE")) t->use_rtab = atoi(v) != 0;
   if (const char* v = getenv("HFMM_OVERLAP_NEAR")) t->overlap_near = atoi(v) != 0;
   if (const char* v = getenv("HFMM_M2L_TC")) t->use_m2l_tcore = atoi(v);

@@ -1918,7 +1918,19 @@ __device__ __forceinline__ void lat_read(const LatSrc<double>& o, double2& q, in
   l = o.lin;
 }
 
-template <typename T, int KMODE>
+// TILE (FP32 only): the staged window is cut into groups of four consecutive
+// staged sources {q0..q3, lin0..lin3}.  When a thread's four targets and a
+// group are both runs of x-consecutive lattice nodes (lin, lin + 1, lin + 2,
+// lin + 3), the 16 pairs use only the seven offsets delta - 3 .. delta + 3,
+// delta = lin_t0 - lin_s0: seven table reads instead of sixteen; other
+// groups take one table read per pair.  A partial last group is padded with
+// zero weights at the group's first node (always a valid table offset).
+struct LatGrp {
+  float4 q01, q23;  // q0, q1 / q2, q3
+  int4 l;           // lin0 .. lin3
+};
+
+template <typename T, int KMODE, bool TILE = false>
 __global__ void __launch_bounds__(LAT_THREADS, sizeof(T) == 4 ? 2 : 1)
     k_p2p_lat(FmmDev<T> d, const int* __restrict__ near_off, int near_count, int src_set, int tgt_set,
               double2 sig_vol, double2 sig_bnd, const int* __restrict__ list, int nlist,
@@ -2028,22 +2040,102 @@ __global__ void __launch_bounds__(LAT_THREADS, sizeof(T) == 4 ? 2 : 1)
       for (int wb = 0; wb < total; wb += LAT_WS) {
         const int wn = min(LAT_WS, total - wb);
         __syncthreads();
-        for (int e = tid; e < wn; e += LAT_THREADS) {
-          const int g = wb + e;
-          int lo = 0, hi = nnb;  // near leaf of staged source g: last q with nb_pre[q] <= g
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (nb_pre[mid] <= g) lo = mid;
-            else hi = mid;
+        if constexpr (TILE) {
+          LatGrp* sgrp = reinterpret_cast<LatGrp*>(lat_smem + tab_bytes);
+          for (int gi = tid; 4 * gi < wn; gi += LAT_THREADS) {
+            float qx[4], qy[4];
+            int ll[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int e = 4 * gi + jj;
+              if (e < wn) {
+                const int g = wb + e;
+                int lo = 0, hi = nnb;
+                while (hi - lo > 1) {
+                  const int mid = (lo + hi) >> 1;
+                  if (nb_pre[mid] <= g) lo = mid;
+                  else hi = mid;
+                }
+                const int j = nb_lo[lo] + (g - nb_pre[lo]);
+                const C<T> qj = d.qs[j];
+                qx[jj] = qj.x;
+                qy[jj] = qj.y;
+                ll[jj] = lin[j];
+              } else {
+                qx[jj] = 0.f;
+                qy[jj] = 0.f;
+                ll[jj] = ll[0];
+              }
+            }
+            LatGrp G;
+            G.q01 = make_float4(qx[0], qy[0], qx[1], qy[1]);
+            G.q23 = make_float4(qx[2], qy[2], qx[3], qy[3]);
+            G.l = make_int4(ll[0], ll[1], ll[2], ll[3]);
+            sgrp[gi] = G;
           }
-          const int j = nb_lo[lo] + (g - nb_pre[lo]);
-          lat_stage(ssrc[e], d.qs[j], lin[j]);
+        } else {
+          for (int e = tid; e < wn; e += LAT_THREADS) {
+            const int g = wb + e;
+            int lo = 0, hi = nnb;  // near leaf of staged source g: last q with nb_pre[q] <= g
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (nb_pre[mid] <= g) lo = mid;
+              else hi = mid;
+            }
+            const int j = nb_lo[lo] + (g - nb_pre[lo]);
+            lat_stage(ssrc[e], d.qs[j], lin[j]);
+          }
         }
         __syncthreads();
         C<T> part[NT];
 #pragma unroll
         for (int j = 0; j < NT; ++j) part[j] = mkc<T>(0, 0);
-        if (active) {
+        if constexpr (TILE) {
+          static_assert(sizeof(T) == 4, "the tiled near field is the FP32 form's");
+          const LatGrp* sgrp = reinterpret_cast<const LatGrp*>(lat_smem + tab_bytes);
+          const bool tcons = lt[1] == lt[0] + 1 && lt[2] == lt[0] + 2 && lt[3] == lt[0] + 3;
+          const int ngw = active ? (wn + 3) >> 2 : 0;
+          for (int gi = sub; gi < ngw; gi += tpt) {
+            const float4 a = sgrp[gi].q01, b = sgrp[gi].q23;
+            const int4 l4 = sgrp[gi].l;
+            const C<T> q[4] = {mkc<T>(a.x, a.y), mkc<T>(a.z, a.w), mkc<T>(b.x, b.y), mkc<T>(b.z, b.w)};
+            if (tcons && l4.y == l4.x + 1 && l4.z == l4.x + 2 && l4.w == l4.x + 3) {
+              // pair (target i, source j): delta = D + i - j -> e[i - j + 3]
+              const int D = lt[0] - l4.x;
+              C<T> e[7];
+#pragma unroll
+              for (int m = 0; m < 7; ++m) e[m] = stab[abs(D + m - 3)];
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const C<T> g = e[i - j + 3];
+                  if constexpr (KMODE == 0) {
+                    part[i].x = fma(g.x, q[j].x, fma(-g.y, q[j].y, part[i].x));
+                    part[i].y = fma(g.x, q[j].y, fma(g.y, q[j].x, part[i].y));
+                  } else {
+                    part[i].x = fma(g.x, q[j].x, fma(g.y, q[j].y, part[i].x));
+                    part[i].y = fma(g.x, q[j].y, fma(-g.y, q[j].x, part[i].y));
+                  }
+                }
+            } else {
+              const int ls[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const C<T> g = stab[abs(lt[i] - ls[j])];
+                  if constexpr (KMODE == 0) {
+                    part[i].x = fma(g.x, q[j].x, fma(-g.y, q[j].y, part[i].x));
+                    part[i].y = fma(g.x, q[j].y, fma(g.y, q[j].x, part[i].y));
+                  } else {
+                    part[i].x = fma(g.x, q[j].x, fma(g.y, q[j].y, part[i].x));
+                    part[i].y = fma(g.x, q[j].y, fma(-g.y, q[j].x, part[i].y));
+                  }
+                }
+            }
+          }
+        } else if (active) {
 #pragma unroll 4
           for (int e = sub; e < wn; e += tpt) {
             C<T> q;
@@ -2306,7 +2398,10 @@ int launch_p2p_lat(fmm_tree* t, const FmmDev<T>& d, int src_set, int tgt_set, do
   const int64_t nh = t->lat_half;  // half-table entries, padded to 16 bytes
   const uint32_t tab_bytes = (uint32_t)(nh * sizeof(C<T>));
   const size_t smem = tab_bytes + (size_t)LAT_WS * sizeof(LatSrc<T>);
-  auto kern = k_p2p_lat<T, KMODE>;
+  auto kern = k_p2p_lat<T, KMODE, false>;
+  if constexpr (sizeof(T) == 4) {
+    if (t->lat_tile) kern = k_p2p_lat<T, KMODE, true>;
+  }
   HFMM_TRY(set_smem<T>((const void*)kern, smem));
   int per_sm = 0;
   HFMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LAT_THREADS, smem));

@@ -209,6 +209,7 @@ struct fmm_tree {
   double2* lat_tab64 = nullptr; // [lat_half] FP64 table
   int lat_tab64_fits = 0;       // the FP64 table fits the near-field kernel's shared memory
   int use_lattice_p2p = 1;      // near field through the table when it exists
+  int lat_tile = 0;             // FP32: 4 x 4 target-source tiles over x-runs of the lattice
 
   // ---- regular basis table [n_pts][P]: R_a(x_i - c) for each sorted point
   //      and its leaf centre (precision of the form); P2M and L2P read it
