@@ -132,3 +132,28 @@ def test_preconditioned_gmres_beats_unpreconditioned():
     _, i1 = gmres.fgmres(A, b, lambda r: pr.precond(r, inner_rtol=1e-4)[0], m=30, rtol=1e-6)
     assert i1["converged"] and i0["converged"]
     assert i1["iters"] * 4 < i0["iters"]
+
+
+def test_single_layer_is_near_singular_at_the_first_cube_eigen_wavenumber():
+    """The single-layer operator of the boundary equation (Eq. (ubound)) is
+    not invertible when k^2 is an interior Dirichlet eigenvalue of the cube
+    (k = pi sqrt(3) = 5.441 for the first mode); the collocated matrix V of
+    the preconditioner's inner solve shows it as a dip of its smallest
+    singular value near that k (shifted by the discretisation), an order of
+    magnitude below its value away from it."""
+    n = 7
+    ks = np.linspace(4.8, 6.2, 29)
+    smin = []
+    for k in ks:
+        pr = bem.Problem(n, k, 4, 64, 0.4)
+        X = pr.x_bnd
+        d = X[:, None, :] - X[None, :, :]
+        r = np.sqrt(np.sum(d * d, axis=-1))
+        np.fill_diagonal(r, 1.0)
+        V = pr.h ** 2 * np.exp(1j * k * r) / (4 * np.pi * r)
+        np.fill_diagonal(V, pr.s_bnd)
+        smin.append(np.linalg.svd(V, compute_uv=False)[-1])
+    smin = np.array(smin)
+    i = int(np.argmin(smin))
+    assert abs(ks[i] - np.pi * np.sqrt(3.0)) < 0.03 * np.pi * np.sqrt(3.0)
+    assert smin[i] < 0.1 * min(smin[0], smin[-1])
