@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--inner-rtol", type=float, default=1e-2)
     ap.add_argument("--inner-maxit", type=int, default=20)
+    ap.add_argument("--inner-p", type=int, default=0,
+                    help="expansion order of the inner solve's boundary -> boundary applies "
+                         "(0: the workload's p)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -277,6 +280,8 @@ def run_ours(args, world, rank, local):
 
     t0 = time.perf_counter()
     tree = hfmm.Tree(n, w["k"], w["p"], w["theta"], w["leaf"], args.precision)
+    if args.inner_p:
+        tree.set_inner_order(args.inner_p)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     b_host = inputs.workload_rhs(args.workload)
@@ -545,7 +550,7 @@ def run_ours(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "k": w["k"], "p": w["p"], "leaf": w["leaf"],
                        "theta": w["theta"], "restart": w["restart"], "inner_rtol": args.inner_rtol,
-                       "inner_maxit": args.inner_maxit,
+                       "inner_maxit": args.inner_maxit, "inner_p": args.inner_p or w["p"],
                        "fmm_precision": args.precision,
                        "krylov_precision": ("outer fp64, inner fp32" if args.precision == "fp32" else "fp64"),
                        "l2": "flushed (512 MB write) before every timed step",

@@ -218,6 +218,20 @@ int fmm_precond_apply(fmm_tree* tree, const void* d_r, void* d_z,
                       int* inner_iters, void* stream);
 
 /*
+ * fmm_set_inner_order -- expansion order of the boundary -> boundary FMM
+ * applies inside the preconditioner's inner solve (Pass B of
+ * fmm_precond_apply, gmres_solve, bicgstab_solve, bem_solve_dirichlet).  The
+ * inner solve runs to a loose tolerance (1e-2 in the benchmark), so a lower
+ * order than the tree's p can serve it; Passes A and C keep p.  p_inner = 0
+ * (or the tree's p) uses the tree itself.  Otherwise an auxiliary tree over
+ * the same points with order p_inner is built on `stream` (device memory
+ * held by the handle; its stage times are added to fmm_get_stats).  Drops a
+ * captured preconditioner graph.  Lattice trees only.
+ * Errors: INVALID_ARG (p_inner outside 0..16), UNSUPPORTED, NOMEM, CUDA.
+ */
+int fmm_set_inner_order(fmm_tree* tree, int p_inner, void* stream);
+
+/*
  * bem_solve_dirichlet -- the BEM solution of -Lap u - k^2 u = f in the cube
  * with Dirichlet data u = u_Gamma on the boundary (Sec. 5.2-5.3: Eq. (ubound)
  * for q = du/dn, then Eq. (uinter) at the interior nodes), every sum by the

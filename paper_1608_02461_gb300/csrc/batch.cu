@@ -79,6 +79,7 @@ extern "C" int fmm_autotune(fmm_tree* t, void* stream) {
     t->tuned_fill[ci] = bf;
   }
   t->timer.on = timer_was_on;
+  if (t->inner) return fmm_autotune(t->inner, stream);  // the inner solve's tree
   return HFMM_OK;
 }
 

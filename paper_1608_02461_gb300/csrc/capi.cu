@@ -49,6 +49,20 @@ inline double2* bnd_q(fmm_tree* t, double) { return t->q_bnd; }
 inline float2* bnd_g(fmm_tree* t, float) { return t->g_bnd32; }
 inline float2* bnd_q(fmm_tree* t, float) { return t->q_bnd32; }
 
+// tree of the boundary -> boundary applies of the inner solve (Pass B), with
+// the caller's timing state (and, while a graph is captured, its timer slots
+// and skip flag)
+inline fmm_tree* pass_b_tree(fmm_tree* t) {
+  fmm_tree* b = t->inner ? t->inner : t;
+  if (b != t) {
+    b->timer.on = t->timer.on;
+    b->timer.mask = t->timer.mask;
+    b->timer.cap = t->timer.cap;
+    b->skip = t->skip;
+  }
+  return b;
+}
+
 static void prec_graph_drop(PrecGraph& G) {
   if (G.exec) cudaGraphExecDestroy(G.exec);
   G.exec = nullptr;
@@ -275,6 +289,7 @@ extern "C" void fmm_destroy_tree(fmm_tree* tree) {
   bicg_work_free(e->bicg);
   prec_graph_drop(e->pg);
   if (e->pg.cap) cudaStreamDestroy(e->pg.cap);
+  if (tree->inner) fmm_destroy_tree(tree->inner);
   release(tree);
   delete e;
   delete tree;
@@ -396,10 +411,11 @@ static int precond_impl_t(fmm_tree* t, const double2* r, double2* z, double inne
   // inner solve V q = -g with V x = h^2 G_{Gamma,Gamma} x + s_Gamma x (Pass B),
   // written as (-V) q = g
   HFMM_TRY(gmres_work_reserve(W, t->n_bnd, inner_m, false));
-  DevOpT<R> negV = [t, h2, s](const C<R>* in, C<R>* out) -> int {
-    HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, in, -h2, s));
-    HFMM_TRY(fmm_core(t, HFMM_SET_BND, HFMM_SET_BND, s));
-    return fmm_scatter(t, HFMM_SET_BND, nullptr, out, s);
+  fmm_tree* tb = pass_b_tree(t);
+  DevOpT<R> negV = [tb, h2, s](const C<R>* in, C<R>* out) -> int {
+    HFMM_TRY(fmm_gather(tb, HFMM_SET_BND, nullptr, 0.0, in, -h2, s));
+    HFMM_TRY(fmm_core(tb, HFMM_SET_BND, HFMM_SET_BND, s));
+    return fmm_scatter(tb, HFMM_SET_BND, nullptr, out, s);
   };
   HFMM_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(C<R>) * t->n_bnd, s));
   GmresResult ir;
@@ -443,10 +459,11 @@ static int bem_dirichlet_impl_t(fmm_tree* t, const double2* f, const double2* ub
   HFMM_TRY(hfmm_last_launch());
   // (-V) q = g
   HFMM_TRY(gmres_work_reserve(W, t->n_bnd, inner_m, false));
-  DevOpT<R> negV = [t, h2, s](const C<R>* in, C<R>* out) -> int {
-    HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, in, -h2, s));
-    HFMM_TRY(fmm_core(t, HFMM_SET_BND, HFMM_SET_BND, s));
-    return fmm_scatter(t, HFMM_SET_BND, nullptr, out, s);
+  fmm_tree* tb = pass_b_tree(t);
+  DevOpT<R> negV = [tb, h2, s](const C<R>* in, C<R>* out) -> int {
+    HFMM_TRY(fmm_gather(tb, HFMM_SET_BND, nullptr, 0.0, in, -h2, s));
+    HFMM_TRY(fmm_core(tb, HFMM_SET_BND, HFMM_SET_BND, s));
+    return fmm_scatter(tb, HFMM_SET_BND, nullptr, out, s);
   };
   HFMM_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(C<R>) * t->n_bnd, s));
   GmresResult ir;
@@ -487,14 +504,19 @@ static int prec_graph_body_t(fmm_tree* t, double rtol, int maxit, cudaStream_t c
   HFMM_TRY(fmm_gather(t, HFMM_SET_VOL, G.r_in, h3, none, 0.0, c));
   HFMM_TRY(fmm_core(t, HFMM_SET_VOL, HFMM_SET_BND, c));
   HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, g, c));
-  DevOpT<R> negV = [t, h2, c](const C<R>* in, C<R>* out) -> int {
-    HFMM_TRY(fmm_gather(t, HFMM_SET_BND, nullptr, 0.0, in, -h2, c));
-    HFMM_TRY(fmm_core(t, HFMM_SET_BND, HFMM_SET_BND, c));
-    return fmm_scatter(t, HFMM_SET_BND, nullptr, out, c);
-  };
   t->skip = G.flags;
+  fmm_tree* tb = pass_b_tree(t);
+  DevOpT<R> negV = [tb, h2, c](const C<R>* in, C<R>* out) -> int {
+    HFMM_TRY(fmm_gather(tb, HFMM_SET_BND, nullptr, 0.0, in, -h2, c));
+    HFMM_TRY(fmm_core(tb, HFMM_SET_BND, HFMM_SET_BND, c));
+    return fmm_scatter(tb, HFMM_SET_BND, nullptr, out, c);
+  };
   int st = gmres_cycle_device<R>(W, negV, g, q, maxit, rtol, G.flags, G.flags + 1, G.flags + 2, c);
   t->skip = nullptr;
+  if (tb != t) {
+    tb->skip = nullptr;
+    tb->timer.cap = nullptr;
+  }
   HFMM_TRY(st);
   HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, G.r_in, h3, q, h2, c));
   HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, c));
@@ -751,6 +773,15 @@ extern "C" int fmm_get_stats(const fmm_tree* t, hfmm_stats* st) {
     st->stage_launches[i] = tt->timer.launches[i];
     st->stage_work[i] = tt->timer.work[i];
   }
+  if (tt->inner) {  // stages of the inner solve's applies timed eagerly on the auxiliary tree
+    tt->inner->timer.flush();
+    for (int i = 0; i < HFMM_NSTAGES; ++i) {
+      st->stage_ms[i] += tt->inner->timer.ms[i];
+      st->stage_launches[i] += tt->inner->timer.launches[i];
+      st->stage_work[i] += tt->inner->timer.work[i];
+    }
+    st->device_bytes += tt->inner->device_bytes;
+  }
   return HFMM_OK;
 }
 
@@ -765,5 +796,35 @@ extern "C" int fmm_set_timing(fmm_tree* t, int stage_mask) {
   t->timer.reset();
   t->timer.on = stage_mask != 0;
   t->timer.mask = stage_mask;
+  if (t->inner) {
+    t->inner->timer.reset();
+    t->inner->timer.on = t->timer.on;
+    t->inner->timer.mask = stage_mask;
+  }
+  return HFMM_OK;
+}
+
+extern "C" int fmm_set_inner_order(fmm_tree* t, int p_inner, void* stream) {
+  if (!t || p_inner < 0 || p_inner > HFMM_MAX_P) return HFMM_ERR_INVALID_ARG;
+  if (p_inner != 0 && p_inner != t->p && !t->lattice) return HFMM_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  prec_graph_drop(ext_of(t)->pg);  // the captured inner solve used the previous tree
+  if (t->inner) {
+    fmm_destroy_tree(t->inner);
+    t->inner = nullptr;
+  }
+  t->inner_p = 0;
+  if (p_inner == 0 || p_inner == t->p) return HFMM_OK;
+  hfmm_params prm;
+  prm.p = p_inner;
+  prm.theta = t->theta;
+  prm.leaf_size = t->leaf_size;
+  prm.k = t->k;
+  prm.precision = t->precision;
+  fmm_tree* aux = nullptr;
+  HFMM_TRY(fmm_build_tree(t->n, nullptr, 0, nullptr, 0, &prm, stream, &aux));
+  t->inner = aux;
+  t->inner_p = p_inner;
   return HFMM_OK;
 }

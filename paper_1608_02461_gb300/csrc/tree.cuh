@@ -266,6 +266,11 @@ struct fmm_tree {
   void* phis = nullptr;         // [n_pts] sorted potentials
 
   int use_graphs = 1;           // gmres_solve replays the preconditioner as one CUDA graph
+  // auxiliary tree over the same points with expansion order inner_p, used
+  // for the boundary -> boundary applies of the preconditioner's inner solve
+  // (Pass B); nullptr: Pass B uses this tree
+  fmm_tree* inner = nullptr;
+  int inner_p = 0;
   // device flag read by every FMM kernel: nonzero = return at once (set while
   // capturing the graph of the inner solve, whose late iterations are skipped
   // after convergence); nullptr outside graphs

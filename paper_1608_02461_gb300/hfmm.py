@@ -97,6 +97,7 @@ SIGNATURES = {
                                            ctypes.POINTER(hfmm_gmres_params),
                                            ctypes.POINTER(hfmm_gmres_info), ctypes.c_void_p]),
     "fmm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "fmm_set_inner_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "fmm_use_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hfmm_direct_sum_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
@@ -329,6 +330,11 @@ class Tree:
 
     def autotune(self, stream=None):
         _check(lib().fmm_autotune(self._h, _stream_ptr(stream)), "fmm_autotune")
+
+    def set_inner_order(self, p_inner, stream=None):
+        """fmm_set_inner_order: expansion order of the inner solve's
+        boundary -> boundary applies (0: the tree's own p)."""
+        _check(lib().fmm_set_inner_order(self._h, p_inner, _stream_ptr(stream)), "fmm_set_inner_order")
 
     def stats(self) -> hfmm_stats:
         s = hfmm_stats()

@@ -81,6 +81,7 @@ def test_invalid_arguments_rejected_without_gpu(built_lib):
     assert L.fmm_apply(None, hfmm.SET_BND, 1, None, None, None, None, hfmm.DLP, None) == hfmm.HFMM_ERR_INVALID_ARG
     assert L.hfmm_dirichlet_rhs(None, None, None, None, None) == hfmm.HFMM_ERR_INVALID_ARG
     assert L.bem_solve_dirichlet(None, None, None, None, 1e-2, 20, 20, None, None) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.fmm_set_inner_order(None, 4, None) == hfmm.HFMM_ERR_INVALID_ARG
 
 
 def test_binding_prototypes_match_header_arity():

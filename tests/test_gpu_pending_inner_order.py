@@ -1,0 +1,82 @@
+"""Inner solve at a lower expansion order (fmm_set_inner_order): Passes A and
+C keep the tree's p, the boundary -> boundary applies of the inner solve use
+an auxiliary tree of order p_inner.  Against the oracle's composition of the
+same passes; switched back to 0 the results are the tree's own, bit for bit;
+and the preconditioned solve of the benchmark workload converges in the
+FP32 form with at most 10% more outer iterations.
+
+Not yet run on a GPU: marked gpu_pending (selected only with -m gpu_pending)
+until it has passed on a GB300."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu_pending,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+from oracle import bem, gmres as ogmres  # noqa: E402
+from paper_1608_02461_gb300 import hfmm, inputs  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_inner_order_preconditioner_matches_oracle_composition():
+    n, k, p, pin, leaf, theta = 10, 4.0, 6, 4, 8, 0.4
+    tree = hfmm.Tree(n, k, p, theta, leaf, "fp64")
+    tree.set_inner_order(pin)
+    r = inputs.complex_normal(n ** 3, 71)
+    z, its = tree.precond(torch.from_numpy(r).to(DEV), inner_rtol=1e-13, inner_maxit=300, inner_m=300)
+    pa = bem.Problem(n, k, p, leaf, theta)
+    pb = bem.Problem(n, k, pin, leaf, theta)
+    h = pa.h
+    NO, NG = pa.NO, pa.NG
+    qa = np.zeros(NO + NG, dtype=np.complex128)
+    qa[:NO] = h ** 3 * r
+    g = pa.green(qa, pa.vol, pa.bnd, "fmm")[NO:]
+
+    def V(qb):
+        qq = np.zeros(NO + NG, dtype=np.complex128)
+        qq[NO:] = h ** 2 * qb
+        return pb.green(qq, pb.bnd, pb.bnd, "fmm")[NO:]
+
+    q, info = ogmres.fgmres(V, -g, None, m=300, rtol=1e-13, maxit=300)
+    qa[NO:] = h ** 2 * q
+    zr = pa.green(qa, pa.vol | pa.bnd, pa.vol, "fmm")[:NO]
+    assert rel(z.cpu().numpy(), zr) < 1e-10
+    assert abs(its - info["iters"]) <= 1
+    tree.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_inner_order_zero_restores_the_tree(prec):
+    n, k = 12, 5.0
+    a = hfmm.Tree(n, k, 6, 0.4, 8, prec)
+    b = hfmm.Tree(n, k, 6, 0.4, 8, prec)
+    b.set_inner_order(4)
+    b.set_inner_order(0)
+    rhs = torch.from_numpy(inputs.rhs("uniform_real", n, 72)).to(DEV)
+    xa, ia = a.gmres(rhs, restart=30, rtol=1e-6, inner_rtol=1e-2, inner_maxit=20, inner_m=20)
+    xb, ib = b.gmres(rhs, restart=30, rtol=1e-6, inner_rtol=1e-2, inner_maxit=20, inner_m=20)
+    assert ia.iters == ib.iters and torch.equal(xa, xb)
+    a.close()
+    b.close()
+
+
+def test_inner_order_benchmark_solve():
+    name = "helmholtz_n64_k16_p6"
+    w = inputs.WORKLOADS[name]
+    b = torch.from_numpy(inputs.workload_rhs(name)).to(DEV)
+    kw = dict(restart=w["restart"], rtol=1e-6, inner_rtol=1e-2, inner_maxit=20, inner_m=20)
+    base = hfmm.Tree(w["n"], w["k"], w["p"], w["theta"], w["leaf"], "fp32")
+    low = hfmm.Tree(w["n"], w["k"], w["p"], w["theta"], w["leaf"], "fp32")
+    low.set_inner_order(4)
+    _, i0 = base.gmres(b, **kw)
+    x1, i1 = low.gmres(b, **kw)
+    assert i0.status == 0 and i1.status == 0 and i1.relres_true < 1e-6
+    assert i1.iters <= int(np.ceil(1.1 * i0.iters)) + 1, (i0.iters, i1.iters)
+    base.close()
+    low.close()
