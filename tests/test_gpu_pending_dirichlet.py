@@ -146,3 +146,18 @@ def test_fdm_solve_with_dirichlet_data():
     ue = np.exp(1j * k * pr.x_vol @ dvec)
     assert rel(x0.cpu().numpy(), ue) < 0.05
     tree.close()
+
+
+def test_double_layer_fp32_full_size_tensor_core_levels():
+    """64^3 (L = 4): the volume-target double layer takes the tensor-core M2L
+    at level 4 with dipole multipoles; FP32 against FP64 on all targets."""
+    name = "helmholtz_n64_k16_p6"
+    w = inputs.WORKLOADS[name]
+    n = w["n"]
+    t64 = hfmm.Tree(n, w["k"], w["p"], w["theta"], w["leaf"], "fp64")
+    t32 = hfmm.Tree(n, w["k"], w["p"], w["theta"], w["leaf"], "fp32")
+    mu = inputs.complex_normal(6 * n * n, 322)
+    for tgt in (hfmm.SET_VOL, hfmm.SET_BND):
+        assert rel(gpu_dlp(t32, mu, tgt), gpu_dlp(t64, mu, tgt)) < 5e-5, tgt
+    t64.close()
+    t32.close()
