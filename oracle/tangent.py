@@ -1,12 +1,14 @@
-"""Tangent (d/dk) of the truncated FMM (oracle, FP64).
+"""Tangent (d/dk) and adjoint of the truncated FMM (oracle, FP64).
 
 TEST INFRASTRUCTURE ONLY (see the package header): only tests/ use it.
 
-The differentiation form of the build asks for dphi/dk of the FMM apply of
-Sec. 5.1.2 (Helmholtz kernel of Sec. 5.2), checked against the oracle.  The
-truncated FMM is a fixed sequence of linear stages whose coefficients depend
-on k, so its exact k-derivative follows every stage by the product rule, in
-the order of the forward pass (readings F1-F3 for the expansions):
+The differentiation form of the build asks for dphi/dk and for the adjoint
+(conjugate transpose) of the FMM apply of Sec. 5.1.2 (Helmholtz kernel of
+Sec. 5.2), checked against the oracle.  The truncated FMM is a fixed sequence
+of linear stages whose coefficients depend on k.  Its adjoint takes every
+stage conjugate-transposed in reverse order (apply_adjoint); its exact
+k-derivative follows every stage by the product rule, in the order of the
+forward pass (readings F1-F3 for the expansions):
 
   P2M    M_a   = sum_j q_j conj(R_a(y_j - c)),      dM_a = sum_j q_j conj(dR_a/dk)
   M2M    M_par = T M_ch,                            dM_par = dT M_ch + T dM_ch
@@ -186,3 +188,95 @@ def apply_dk(fmm: FMM, q, src_mask, tgt_mask, dsigma):
     # self terms
     dphi[tgt_mask] += np.where(src_mask[tgt_mask], dsigma[tgt_mask] * q[tgt_mask], 0.0)
     return dphi
+
+
+def apply_adjoint(fmm: FMM, y, src_mask, tgt_mask, sigma):
+    """Conjugate transpose of FMM.apply(., src_mask, tgt_mask, sigma): the
+    weights y live on the targets, the result on the sources.  Every stage of
+    Sec. 5.1.2 conjugate-transposed, in reverse order:
+
+      L2P^H   Lh_a(leaf) = sum_i conj(i k R_a(x_i - c)) y_i
+      L2L^H   Lh_par    += sum_children T^H Lh_child          (upward)
+      M2L^H   Mh_S      += sum_{T: S in list(T)} T_v^H Lh_T
+      M2M^H   Mh_child   = T^H Mh_par                          (downward)
+      P2M^H   out_j      = sum_a R_a(y_j - c) Mh_a
+      P2P^H   out_j     += sum_{i near, i != j} conj(G(x_i, x_j)) y_i
+      self    out_j     += conj(sigma_j) y_j
+    """
+    k, p, P, L = fmm.k, fmm.p, fmm.P, fmm.L
+    tr = fmm.tree
+    out = np.zeros(len(tr.points), dtype=np.complex128)
+    # L2P^H
+    Lh = {l: np.zeros((8 ** l, P), dtype=np.complex128) for l in range(2, L + 1)}
+    i = np.flatnonzero(tgt_mask)
+    if len(i):
+        leaf = tr.leaf[i]
+        c = centres(L)[leaf]
+        R = S.regular_all(p, k, tr.points[i] - c)
+        np.add.at(Lh[L], leaf, (np.conj(1j * k * R) * y[i][None, :]).T)
+    # L2L^H, levels L-1 .. 2 (children at l + 1 feed their parent at l)
+    for l in range(L - 1, 1, -1):
+        s = 2 ** l
+        g = np.arange(s)
+        iz, iy, ix = np.meshgrid(g, g, g, indexing="ij")
+        I = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1)
+        wc = fmm.w(l + 1)
+        for o in np.ndindex(2, 2, 2):
+            o = np.array(o)
+            T = TT.l2l_op(p, k, (o - 0.5) * wc)
+            child = flat(2 * I + o, l + 1)
+            Lh[l][flat(I, l)] += Lh[l + 1][child] @ np.conj(T)
+    # M2L^H
+    Mh = {l: np.zeros((8 ** l, P), dtype=np.complex128) for l in range(2, L + 1)}
+    for l in range(2, L + 1):
+        for v, (t_idx, s_idx) in tr.m2l_pairs(l).items():
+            T = TT.m2l_op(p, k, -np.array(v, dtype=np.float64) * fmm.w(l))
+            np.add.at(Mh[l], s_idx, Lh[l][t_idx] @ np.conj(T))
+    # M2M^H, levels 2 .. L-1 (parent at l feeds its children at l + 1)
+    for l in range(2, L):
+        s = 2 ** l
+        g = np.arange(s)
+        iz, iy, ix = np.meshgrid(g, g, g, indexing="ij")
+        I = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1)
+        wc = fmm.w(l + 1)
+        for o in np.ndindex(2, 2, 2):
+            o = np.array(o)
+            T = TT.m2m_op(p, k, (0.5 - o) * wc)
+            child = flat(2 * I + o, l + 1)
+            Mh[l + 1][child] += Mh[l][flat(I, l)] @ np.conj(T)
+    # P2M^H
+    j = np.flatnonzero(src_mask)
+    if len(j):
+        leaf = tr.leaf[j]
+        c = centres(L)[leaf]
+        R = S.regular_all(p, k, tr.points[j] - c)
+        out[j] += np.sum(R * Mh[L][leaf].T, axis=0)
+    # P2P^H: for every source leaf, the targets of its near leaves
+    s = 2 ** L
+    src = np.flatnonzero(src_mask)
+    tgt = np.flatnonzero(tgt_mask)
+    tgt_by_leaf, src_by_leaf = {}, {}
+    for ii, lf in zip(tgt, tr.leaf[tgt]):
+        tgt_by_leaf.setdefault(int(lf), []).append(ii)
+    for jj, lf in zip(src, tr.leaf[src]):
+        src_by_leaf.setdefault(int(lf), []).append(jj)
+    near = np.array(tr.near)
+    for lf, sj in src_by_leaf.items():
+        sj = np.array(sj)
+        cc = tr.leaf_c[sj[0]]
+        nb = cc + near
+        ok = np.all((nb >= 0) & (nb < s), axis=1)
+        ti = [tgt_by_leaf.get(int(f), []) for f in flat(nb[ok], L)]
+        ti = np.array([x for lst in ti for x in lst], dtype=np.int64)
+        if len(ti) == 0:
+            continue
+        d = tr.points[ti][:, None, :] - tr.points[sj][None, :, :]
+        r = np.sqrt(np.sum(d * d, axis=-1))
+        same = ti[:, None] == sj[None, :]
+        r = np.where(same, 1.0, r)
+        G = np.where(same, 0.0, np.exp(1j * k * r) / (4 * pi * r))
+        out[sj] += np.conj(G).T @ y[ti]
+    # self terms
+    both = src_mask & tgt_mask
+    out[both] += np.conj(sigma[both]) * y[both]
+    return out

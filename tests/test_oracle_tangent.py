@@ -1,7 +1,9 @@
-"""Pins for the oracle's tangent (d/dk) FMM: every piece against
-finite differences in k of the oracle's own forward pieces (five-point
-stencil, step 1e-3: truncation ~1e-13), and the self-term derivatives at
-k = 0 against their closed forms."""
+"""Pins for the oracle's tangent (d/dk) and adjoint FMM.  Tangent: every
+piece against finite differences in k of the oracle's own forward pieces
+(five-point stencil, step 1e-3: truncation ~1e-13), and the self-term
+derivatives at k = 0 against their closed forms.  Adjoint: the dot-product
+identity <G x, y> = <x, G^H y> with the forward oracle FMM, and the conjugate
+transpose of the assembled forward matrix on a tiny tree."""
 from math import pi
 
 import numpy as np
@@ -90,3 +92,34 @@ def test_tangent_fmm_set_masks_and_linearity():
     d_v = TG.apply_dk(pr.fmm, q, pr.vol, pr.vol, ds)
     d_b = TG.apply_dk(pr.fmm, q, pr.bnd, pr.vol, ds)
     assert np.allclose(d_v + d_b, d_all, rtol=1e-12, atol=1e-12 * np.abs(d_all).max())
+
+
+@pytest.mark.parametrize("sets", ["all", "vol_to_bnd", "bnd_to_vol"])
+def test_adjoint_dot_product_identity(sets):
+    n, k, p, leaf = 8, 5.0, 5, 8
+    pr = bem.Problem(n, k, p, leaf, 0.4)
+    N = pr.NO + pr.NG
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    y = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    sm, tm = {"all": (pr.vol | pr.bnd, pr.vol | pr.bnd), "vol_to_bnd": (pr.vol, pr.bnd),
+              "bnd_to_vol": (pr.bnd, pr.vol)}[sets]
+    Gx = pr.fmm.apply(np.where(sm, x, 0), sm, tm, pr.sigma)
+    GHy = TG.apply_adjoint(pr.fmm, np.where(tm, y, 0), sm, tm, pr.sigma)
+    assert np.all(GHy[~sm] == 0)
+    lhs = np.vdot(y[tm], Gx[tm])
+    rhs = np.vdot(GHy[sm], x[sm])
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+def test_adjoint_is_the_conjugate_transpose():
+    n, k, p, leaf = 4, 3.0, 4, 4
+    pr = bem.Problem(n, k, p, leaf, 0.4)
+    N = pr.NO + pr.NG
+    allm = np.ones(N, bool)
+    G = np.stack([pr.fmm.apply(e, allm, allm, pr.sigma) for e in np.eye(N, dtype=np.complex128)], axis=1)
+    rng = np.random.default_rng(4)
+    y = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    got = TG.apply_adjoint(pr.fmm, y, allm, allm, pr.sigma)
+    ref = G.conj().T @ y
+    assert np.linalg.norm(got - ref) < 1e-13 * np.linalg.norm(ref)
