@@ -11,5 +11,3 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds")
-    config.addinivalue_line("markers", "gpu_pending: GPU parity test written but not yet run on a GPU; "
-                                       "selected only with -m gpu_pending, promoted to gpu once it has passed")

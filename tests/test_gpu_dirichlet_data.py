@@ -1,7 +1,5 @@
 """GPU parity tests for Dirichlet data (paper Sec. 5.2-5.3, Eq. (ubound) and
-Eq. (uinter) with boundary data) that have not yet run on a GPU: marked
-gpu_pending, selected only with `-m gpu_pending`, and moved to gpu once they
-have passed on a GB300.  Against the FP64 oracle, through the C ABI: the
+Eq. (uinter) with boundary data).  Against the FP64 oracle, through the C ABI: the
 double layer at high order, in FP32 and on an L = 2 tree whose panels lie on
 the polar axis of their leaf centre; the FDM right-hand side with Dirichlet
 data (hfmm_dirichlet_rhs); the BEM solution with data (bem_solve_dirichlet);
@@ -10,7 +8,7 @@ import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu_pending,
+pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
 from oracle import dirichlet, fdm  # noqa: E402

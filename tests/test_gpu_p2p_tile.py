@@ -3,15 +3,12 @@ over x-runs of lattice nodes, switch HFMM_P2P_TILE=1) against the untiled
 form, for every pass, in forward and adjoint mode, on trees whose leaves are
 4 x 4 x 4 blocks of nodes (all tiles take the seven-read path) and on ragged
 ones (rows of 3 or 5 nodes: the per-pair path), and one preconditioned solve.
-Both forms sum the same FP32 products in a different order.
-
-Not yet run on a GPU: marked gpu_pending (selected only with -m gpu_pending)
-until it has passed on a GB300."""
+Both forms sum the same FP32 products in a different order."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu_pending,
+pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
 from paper_1608_02461_gb300 import hfmm, inputs  # noqa: E402

@@ -1,13 +1,11 @@
 """GPU parity of the tangent and adjoint modes (fmm_apply HFMM_DK, HFMM_ADJ)
 against the oracle's exact tangent and stage-by-stage adjoint FMM
-(oracle.tangent.apply_dk, apply_adjoint), FP64, 1e-11 relative L2.  Not yet
-run on a GPU: marked gpu_pending (selected only with -m gpu_pending) until it
-has passed on a GB300."""
+(oracle.tangent.apply_dk, apply_adjoint), FP64, 1e-11 relative L2."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu_pending,
+pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
 from oracle import bem, tangent  # noqa: E402
