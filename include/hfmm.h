@@ -365,6 +365,29 @@ int fmm_get_stats(const fmm_tree* tree, hfmm_stats* stats);
 int fmm_set_timing(fmm_tree* tree, int stage_mask);
 
 /*
+ * hfmm_pipe_peaks -- measured throughput of the arithmetic pipes that bound
+ * the solver's kernels (the roofline denominators; no counterpart in the
+ * paper).  Runs one short kernel per pipe on the current device, on every SM,
+ * and reports the best of three launches timed with CUDA events; the clocks
+ * are whatever the GPU runs at.  Takes about 50 ms.
+ *   out[HFMM_PEAK_FP32_TFLOPS]  FP32 FMA, 2 flop per FMA
+ *   out[HFMM_PEAK_FP64_TFLOPS]  FP64 FMA, 2 flop per FMA
+ *   out[HFMM_PEAK_XU_GOPS]      multi-function unit ops (sin, cos, rsqrt) per second, 1e9
+ *   out[HFMM_PEAK_SMEM_GBS]     shared-memory 16-byte loads, GB/s
+ *   out[HFMM_PEAK_TF32_TFLOPS]  tcgen05.mma kind::tf32 (M 128, N 256), dense, 2 flop per MAC
+ * out is a host array of HFMM_NPEAKS doubles.  Allocates 64 bytes of device
+ * memory for the duration of the call.  Returns HFMM_ERR_TIMEOUT if the
+ * tensor-core probe's bounded wait gave up.
+ */
+#define HFMM_PEAK_FP32_TFLOPS 0
+#define HFMM_PEAK_FP64_TFLOPS 1
+#define HFMM_PEAK_XU_GOPS     2
+#define HFMM_PEAK_SMEM_GBS    3
+#define HFMM_PEAK_TF32_TFLOPS 4
+#define HFMM_NPEAKS           5
+int hfmm_pipe_peaks(double* out, void* stream);
+
+/*
  * hfmm_direct_sum_noalloc -- allocation-free direct Helmholtz sum.
  *
  * The paper has no counterpart to this entry point.  It exists for callers
@@ -385,9 +408,13 @@ int fmm_set_timing(fmm_tree* tree, int stage_mask);
  * min(32, 262144 / n_tgt) chunks.  FP64 arithmetic, deterministic.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) for that device; make that first call before any
- * stream capture.  Calls share the scratch array, so calls that overlap on
- * the GPU (different streams, or different host threads on one device) race
- * and must be serialised by the caller.  Every scratch entry a call reads is
+ * stream capture (a first call made while its stream is being captured
+ * returns HFMM_ERR_UNSUPPORTED).  Calls on a stream that is not being
+ * captured look the address up again, so a device reset between such calls
+ * leaves no stale address behind.
+ * Calls share the scratch array, so calls that overlap on the GPU (different
+ * streams, or different host threads on one device) race and must be
+ * serialised by the caller.  Every scratch entry a call reads is
  * written earlier in the same call, so no clearing is needed.
  */
 int hfmm_direct_sum_noalloc(int64_t n_src, const double* d_src_xyz, const void* d_q,

@@ -88,13 +88,22 @@ __global__ void k_direct_reduce(int64_t n_tgt, int nchunks, const double2* __res
   phi[i] = s;
 }
 
-// device address of the scratch array for the current device (set-up on the
-// first call on each device)
-int scratch_for_current_device(double2** out) {
+// device address of the scratch array for the current device.  The first
+// call on each device looks it up (a first call on a stream that is being
+// captured is refused); later calls on a stream that is not being captured
+// look it up again, because a device reset or a recreated primary context
+// moves the array and a cached address would then be stale.
+int scratch_for_current_device(cudaStream_t s, double2** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HFMM_ERR_CUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;  // unknown: do not call the runtime's symbol lookup
+  }
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || cap == cudaStreamCaptureStatusNone) {
+    if (cap != cudaStreamCaptureStatusNone) return HFMM_ERR_UNSUPPORTED;  // first call inside a capture
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -122,9 +131,9 @@ extern "C" int hfmm_direct_sum_noalloc(int64_t n_src, const double* d_src_xyz, c
   if (nchunks > kMaxChunks) nchunks = kMaxChunks;
   if (nchunks * n_tgt > kScratchEntries) nchunks = kScratchEntries / n_tgt;
   const int64_t chunk_len = n_src > 0 ? (n_src + nchunks - 1) / nchunks : 1;
-  double2* scratch = nullptr;
-  HFMM_TRY(scratch_for_current_device(&scratch));
   cudaStream_t s = (cudaStream_t)stream;
+  double2* scratch = nullptr;
+  HFMM_TRY(scratch_for_current_device(s, &scratch));
   dim3 grid(ceil_div(n_tgt, kThreads), (unsigned)nchunks);
   k_direct_chunk<<<grid, kThreads, 0, s>>>(n_src, d_src_xyz, (const double2*)d_q, n_tgt, d_tgt_xyz, k,
                                            chunk_len, scratch);

@@ -102,7 +102,11 @@ SIGNATURES = {
     "hfmm_direct_sum_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "hfmm_pipe_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
 }
+
+# order of hfmm_pipe_peaks' outputs
+PEAKS = ("fp32_tflops", "fp64_tflops", "xu_gops", "smem_gbs", "tf32_tflops")
 
 # scratch limit of hfmm_direct_sum_noalloc (targets)
 NOALLOC_MAX_TARGETS = 1 << 18
@@ -369,10 +373,49 @@ def gmres_solve_batched(trees, bs, xs=None, restart=50, rtol=1e-6, maxit=0, inne
     return xs, out
 
 
+def check_noalloc_args(src_xyz, q, tgt_xyz, phi, require_cuda=True):
+    """Argument checks of direct_sum_noalloc, made before anything is launched:
+    both coordinate arrays contiguous float64 of shape (n, 3); q and phi
+    contiguous complex128 with n_src and n_tgt entries; every tensor a CUDA
+    tensor on one device (require_cuda=False skips the device checks, for
+    host-side tests of the others).  Raises ValueError."""
+    torch = _torch()
+    for name, t in (("src_xyz", src_xyz), ("tgt_xyz", tgt_xyz)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.dim() != 2 \
+                or t.shape[1] != 3 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 tensor of shape (n, 3)")
+    n_src, n_tgt = src_xyz.shape[0], tgt_xyz.shape[0]
+    for name, t, n in (("q", q, n_src), ("phi", phi, n_tgt)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or t.dim() != 1 \
+                or t.numel() != n or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous complex128 tensor with {n} entries")
+    if n_tgt > NOALLOC_MAX_TARGETS:
+        raise ValueError(f"at most {NOALLOC_MAX_TARGETS} targets per call (got {n_tgt})")
+    if require_cuda:
+        devs = {t.device for t in (src_xyz, q, tgt_xyz, phi)}
+        if len(devs) != 1 or not all(t.is_cuda for t in (src_xyz, q, tgt_xyz, phi)):
+            raise ValueError("src_xyz, q, tgt_xyz and phi must be CUDA tensors on one device")
+    return n_src, n_tgt
+
+
 def direct_sum_noalloc(src_xyz, q, tgt_xyz, k, phi, stream=None):
     """Allocation-free direct sum (hfmm_direct_sum_noalloc) into the caller's
-    complex128 tensor `phi`; all arguments are CUDA tensors."""
-    st = lib().hfmm_direct_sum_noalloc(src_xyz.shape[0], _ptr(src_xyz), _ptr(q), tgt_xyz.shape[0],
-                                       _ptr(tgt_xyz), float(k), _ptr(phi), _stream_ptr(stream))
+    complex128 tensor `phi`; all arguments are CUDA tensors on one device,
+    checked before the call."""
+    n_src, n_tgt = check_noalloc_args(src_xyz, q, tgt_xyz, phi)
+    if not (float(k) >= 0.0):
+        raise ValueError("k must be >= 0")
+    torch = _torch()
+    with torch.cuda.device(phi.device):
+        st = lib().hfmm_direct_sum_noalloc(n_src, _ptr(src_xyz), _ptr(q), n_tgt, _ptr(tgt_xyz), float(k),
+                                           _ptr(phi), _stream_ptr(stream))
     _check(st, "hfmm_direct_sum_noalloc")
     return phi
+
+
+def pipe_peaks(stream=None):
+    """hfmm_pipe_peaks: measured pipe rates of the current device, as a dict
+    keyed by PEAKS (TFLOP/s, TFLOP/s, 1e9 XU ops/s, GB/s, TFLOP/s)."""
+    out = (ctypes.c_double * len(PEAKS))()
+    _check(lib().hfmm_pipe_peaks(out, _stream_ptr(stream)), "hfmm_pipe_peaks")
+    return {name: out[i] for i, name in enumerate(PEAKS)}

@@ -96,3 +96,41 @@ def test_binding_prototypes_match_header_arity():
         assert m, name
         params = [p for p in m.group(1).split(",") if p.strip() and p.strip() != "void"]
         assert len(params) == len(args), (name, len(params), len(args))
+
+
+def test_noalloc_binding_rejects_bad_arguments_before_launch():
+    """direct_sum_noalloc checks dtype, shape, length, contiguity and device of
+    every tensor before it calls the library (nothing here reaches a GPU)."""
+    torch = pytest.importorskip("torch")
+    from paper_1608_02461_gb300 import hfmm
+    n_src, n_tgt = 5, 3
+    good = dict(src_xyz=torch.zeros(n_src, 3, dtype=torch.float64),
+                q=torch.zeros(n_src, dtype=torch.complex128),
+                tgt_xyz=torch.zeros(n_tgt, 3, dtype=torch.float64),
+                phi=torch.zeros(n_tgt, dtype=torch.complex128))
+    assert hfmm.check_noalloc_args(**good, require_cuda=False) == (n_src, n_tgt)
+    bad = [
+        ("q", torch.zeros(n_src, dtype=torch.complex64)),                 # complex64 weights
+        ("q", torch.zeros(n_src + 1, dtype=torch.complex128)),            # wrong length
+        ("q", torch.zeros(2 * n_src, dtype=torch.complex128)[::2]),       # non-contiguous view
+        ("phi", torch.zeros(n_tgt - 1, dtype=torch.complex128)),          # phi shorter than the targets
+        ("phi", torch.zeros(n_tgt, dtype=torch.complex64)),
+        ("src_xyz", torch.zeros(n_src, 3, dtype=torch.float32)),          # float32 coordinates
+        ("src_xyz", torch.zeros(3, n_src, dtype=torch.float64).t()),      # transposed view
+        ("tgt_xyz", torch.zeros(n_tgt, 2, dtype=torch.float64)),          # not (n, 3)
+        ("tgt_xyz", torch.zeros(3 * n_tgt, dtype=torch.float64)),         # flat
+    ]
+    for name, t in bad:
+        args = dict(good)
+        args[name] = t
+        with pytest.raises(ValueError):
+            hfmm.check_noalloc_args(**args, require_cuda=False)
+    # host tensors are refused before the library is called
+    with pytest.raises(ValueError):
+        hfmm.direct_sum_noalloc(good["src_xyz"], good["q"], good["tgt_xyz"], 1.0, good["phi"])
+    # more targets than the scratch array holds
+    big = hfmm.NOALLOC_MAX_TARGETS + 1
+    args = dict(good, tgt_xyz=torch.zeros(big, 3, dtype=torch.float64),
+                phi=torch.zeros(big, dtype=torch.complex128))
+    with pytest.raises(ValueError):
+        hfmm.check_noalloc_args(**args, require_cuda=False)
