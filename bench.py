@@ -10,12 +10,17 @@ outer GMRES in FP64.  The tree and operators are built before the timed
 region (reported as build_s).
 
 Printed JSON line (rank 0):
-  value        seconds per solve (time-to-1e-6, device time, inputs resident)
+  value        seconds per solve (time-to-1e-6, device time, inputs resident),
+               K solves with no instrumentation
   e2e          the same through host buffers (H2D of f, D2H of u inside)
-  roofline     the near-field kernel (largest share of device time), from live
-               CUDA-event timers around its launches in the timed region
+  roofline     the near-field kernel (largest share of device time): live
+               CUDA-event timers around its launches over a second pass of the
+               K solves, 23 flop-equivalents per pair against the FP32 FMA
+               rate measured by hfmm_pipe_peaks; per pass beside it
+  pipe_peaks   the measured pipe rates (FP32, FP64, XU, shared memory, TF32)
   cpu_baseline the FP64 CPU oracle on a bounded sample, scaled to one solve
   fp64         the plain FP64 form of the same solve (time, iterations)
+  n128         one FP32 solve of the 128^3, k = 32, p = 8 workload
   bicgstab     BiCGSTAB with the same preconditioner (time, iterations, applies)
   fmm_apply_mpts_s  (N_vol + N_bnd) / time of one full FMM apply (FP32 form)
 
@@ -41,15 +46,17 @@ if ROOT not in sys.path:
 METRIC = "GMRES time-to-1e-6 and FMM apply Mpts/s: FP32/batched vs plain FP64, same GB300"
 WORKLOAD = "helmholtz_n64_k16_p6"
 
-# GB300: 152 SMs, 128 FP32 lanes per SM, 2 flop per FMA, 2070 MHz maximum SM clock
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 rate (vendor figure)
-P2P_FLOP_PER_PAIR = 8       # lattice-table near field: one complex multiply-add per pair
-# The FP32 lattice near-field kernel reads, per 32 pairs, one 32-lane 8-byte
-# table load (2 shared-memory wavefronts) and one broadcast source load
-# (1 wavefront); at one 128-byte wavefront per SM per clock its ceiling is
-# 152 SM x 2.07 GHz x 32/3 pairs per clock, expressed in its 8 flop per pair.
-P2P_SMEM_PEAK_TFLOPS = 152 * 2.070e9 * 32 / 3 * P2P_FLOP_PER_PAIR / 1e12
+# Algorithmic work of one near-field pair, as a direct evaluation counts it:
+# 3 subtractions, 5 for r^2, 1 rsqrt, 1 for r, 1 for kr, sin + cos, 2 for G,
+# 6 for the complex product with q, 2 for the accumulation: about 23
+# flop-equivalents (3 of them XU ops).  The roofline divides 23 x pairs/s by
+# the measured FP32 (FP64) FMA rate, the busiest pipe of that evaluation.
+P2P_FLOP_EQ_PER_PAIR = 23
+P2P_XU_OPS_PER_PAIR = 3
+# The FP32 lattice kernel replaces that evaluation by a table: per pair one
+# 8-byte table entry and a quarter of a 16-byte staged source record come
+# from shared memory, so shared-memory loads bound it (secondary figure).
+P2P_SMEM_BYTES_PER_PAIR = 12
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_p2p_lat launch (ncu,
 # 64^3 k=16 p=6 FP32 workload) for the three passes of the preconditioner:
 # volume -> boundary, boundary -> boundary, all -> volume
@@ -74,6 +81,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-solve batched measurement")
+    ap.add_argument("--no-big", action="store_true", help="skip the 128^3 solve")
     ap.add_argument("--no-bicgstab", action="store_true", help="skip the BiCGSTAB solve of the same system")
     ap.add_argument("--dirichlet", action="store_true",
                     help="also time the solve with Dirichlet data (plane-wave boundary values): "
@@ -87,17 +95,6 @@ def parse():
                     help="profiling case: build the tree and run two FMM applies with these "
                          "source/target set masks (1 volume, 2 boundary, 3 both), print nothing else")
     return ap.parse_args()
-
-
-def measured_peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(path):
-        try:
-            d = json.load(open(path))
-            return d, "measured"
-        except Exception:
-            pass
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
 class ClockSampler:
@@ -262,6 +259,63 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def p2p_roofline(live, pk, lattice, info, bench_workload):
+    """Roofline object of the near-field kernel from its stage timers: (ms,
+    launches, point pairs) over the timed launches."""
+    sm_, nl_, work_ = live
+    pairs_s = work_ / (sm_ * 1e-3) if sm_ > 0 else 0.0
+    achieved = P2P_FLOP_EQ_PER_PAIR * pairs_s / 1e12
+    peak = pk["fp32_tflops"] if lattice else pk["fp64_tflops"]
+    traffic = None
+    if lattice and bench_workload:
+        na, nb_, nc = info.iters, info.inner_iters_total, info.iters
+        traffic = (na * P2P_DRAM_BYTES["A"] + nb_ * P2P_DRAM_BYTES["B"] + nc * P2P_DRAM_BYTES["C"]) / (na + nb_ + nc)
+    roof = {"bound": "alu", "kernel": "k_p2p_lat", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_kind": "measured",
+            "peak_source": ("FP32" if lattice else "FP64") + " FMA rate measured by hfmm_pipe_peaks",
+            "per_launch_ms": sm_ / max(1, nl_), "work_per_launch": work_ / max(1, nl_),
+            "work_unit": f"point pairs, {P2P_FLOP_EQ_PER_PAIR} flop-equivalents each",
+            "gpair_s": pairs_s / 1e9,
+            "frac_of_xu": P2P_XU_OPS_PER_PAIR * pairs_s / (pk["xu_gops"] * 1e9),
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, weighted by the "
+                               "solve's pass mix") if traffic is not None else None,
+            "source": "CUDA events around every launch of the kernel (on its own stream) over a second pass "
+                      "of the K timed solves; the headline pass runs without them"}
+    if lattice:
+        roof["smem"] = {"bytes_per_pair": P2P_SMEM_BYTES_PER_PAIR,
+                        "achieved_gbs": P2P_SMEM_BYTES_PER_PAIR * pairs_s / 1e9, "peak_gbs": pk["smem_gbs"],
+                        "frac": P2P_SMEM_BYTES_PER_PAIR * pairs_s / (pk["smem_gbs"] * 1e9)}
+    return roof
+
+
+def p2p_per_pass(tree, hfmm, inputs, n, dev, pk, lattice, reps=10):
+    """Near-field rate of each pass of the preconditioner (A: volume ->
+    boundary, B: boundary -> boundary, C: all -> volume) from standalone
+    applies with the near-field stage timed."""
+    import torch
+    peak = pk["fp32_tflops"] if lattice else pk["fp64_tflops"]
+    qv = torch.from_numpy(inputs.complex_normal(n ** 3, 53)).to(dev)
+    qb = torch.from_numpy(inputs.complex_normal(6 * n * n, 54)).to(dev)
+    out = {}
+    for name, src, tgt in (("A", hfmm.SET_VOL, hfmm.SET_BND), ("B", hfmm.SET_BND, hfmm.SET_BND),
+                           ("C", hfmm.SET_VOL | hfmm.SET_BND, hfmm.SET_VOL)):
+        pv, pb = tree.apply(qv, qb, src=src, tgt=tgt)
+        tree.set_timing(True, stages=["p2p"])
+        for _ in range(reps):
+            tree.apply(qv, qb, src=src, tgt=tgt, phi_vol=pv, phi_bnd=pb)
+        torch.cuda.synchronize()
+        ms, nl, work = tree.stage_times()["p2p"]
+        tree.set_timing(False)
+        if nl == 0 or ms <= 0:  # the pass ran as the one-kernel boundary operator
+            out[name] = {"per_launch_ms": None, "note": "near field inside the boundary-operator kernel"}
+            continue
+        pairs_s = work / (ms * 1e-3)
+        out[name] = {"per_launch_ms": ms / max(1, nl), "gpair_s": pairs_s / 1e9,
+                     "achieved": P2P_FLOP_EQ_PER_PAIR * pairs_s / 1e12,
+                     "frac": P2P_FLOP_EQ_PER_PAIR * pairs_s / 1e12 / peak}
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     from __graft_entry__ import build
@@ -304,9 +358,10 @@ def run_ours(args, world, rank, local):
     stages = tree.stage_times()
     tree.set_timing(False)
     dom = "p2p"  # the near-field kernel: the largest share of device time in the launch list
+    pk = hfmm.pipe_peaks()
 
+    # the headline: K solves with no instrumentation
     clocks = ClockSampler(not args.no_clocks and rank == 0, local)
-    tree.set_timing(True, stages=[dom])   # only the dominant stage's launches are bracketed
     launches0 = tree.stats().launches
     if world > 1:
         torch.distributed.barrier()
@@ -328,34 +383,23 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     st = tree.stats()
     launches = st.launches - launches0
-    live = tree.stage_times()
-    tree.set_timing(False)
     ms = sum(a.elapsed_time(c) for a, c in evs) / args.steps
     ms = barrier_max(ms, world, dev)
     info = infos[-1]
     relres = info.relres_true
 
-    # dominant stage and its roofline, from the events of the timed region
-    sm_, nl_, work_ = live[dom]
-    peaks, peak_kind = measured_peaks()
-    flop = work_ * P2P_FLOP_PER_PAIR
-    achieved = flop / (sm_ * 1e-3) / 1e12
+    # the roofline pass: the same K solves again, with CUDA events around
+    # every launch of the near-field kernel (on the stream each launch uses)
+    tree.set_timing(True, stages=[dom])
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        solve()
+    torch.cuda.synchronize()
+    live = tree.stage_times()
+    tree.set_timing(False)
     lattice = args.precision == "fp32"
-    peak = P2P_SMEM_PEAK_TFLOPS if lattice else FP64_PEAK_TFLOPS
-    traffic = None
-    if lattice and args.workload == WORKLOAD:
-        na, nb_, nc = info.iters, info.inner_iters_total, info.iters
-        traffic = (na * P2P_DRAM_BYTES["A"] + nb_ * P2P_DRAM_BYTES["B"] + nc * P2P_DRAM_BYTES["C"]) / (na + nb_ + nc)
-    roof = {"bound": "alu", "kernel": "k_p2p_lat", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "per_launch_ms": sm_ / max(1, nl_), "work_per_launch": work_ / max(1, nl_),
-            "work_unit": "point pairs (8 flop each)", "gpair_s": work_ / (sm_ * 1e-3) / 1e9,
-            "frac_of_fp32_fma_peak": achieved / FP32_ALU_PEAK_TFLOPS,
-            "peak_source": ("shared-memory wavefronts: 152 SM x 2.07 GHz x 32/3 pairs per clock x 8 flop"
-                            if lattice else "nominal FP64 rate (4 DFMA per pair)"),
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                              "weighted by the solve's pass mix" if traffic is not None else None}
-    roof["peak_kind"] = peak_kind if roof["bound"] == "hbm" else "derived"
+    roof = p2p_roofline(live[dom], pk, lattice, info, args.workload == WORKLOAD)
+    roof["per_pass"] = p2p_per_pass(tree, hfmm, inputs, n, dev, pk, lattice)
     stage_summary = {k: {"ms": v[0], "launches": v[1]} for k, v in stages.items()}
     # the far field's M2L stage over one fully timed solve (outside the timed
     # region): algorithmic 8 P^2 flop per cell pair over all its launches
@@ -363,17 +407,18 @@ def run_ours(args, world, rank, local):
     # pipelines and pair lists elsewhere)
     m2l_ms, m2l_nl, m2l_flop = stages["m2l"]
     roof_m2l = None
-    if m2l_ms > 0 and m2l_flop > 0:
+    if m2l_ms > 0 and m2l_flop > 0 and pk is not None:
         a2 = m2l_flop / (m2l_ms * 1e-3) / 1e12
-        p2 = FP32_ALU_PEAK_TFLOPS if lattice else FP64_PEAK_TFLOPS
+        p2 = pk["fp32_tflops"] if lattice else pk["fp64_tflops"]
         roof_m2l = {"bound": "alu", "kernel": "M2L stage (k_m2l_tc, k_m2l_ws, k_m2l_pairs)", "achieved": a2,
                     "peak": p2, "unit": "TFLOP/s", "frac": a2 / p2, "launches": m2l_nl,
                     "ms_per_solve": m2l_ms, "work_unit": "8 P^2 flop per cell pair",
-                    "peak_source": ("FP32 FMA pipes: 152 SM x 128 lanes x 2 flop x 2.07 GHz" if lattice
-                                    else "nominal FP64 rate"),
+                    "peak_kind": "measured",
+                    "peak_source": ("FP32 FMA rate measured by hfmm_pipe_peaks" if lattice
+                                    else "FP64 FMA rate measured by hfmm_pipe_peaks"),
                     # tensor-core M2L in FP32 accuracy: three TF32 products per
-                    # algorithmic one; TF32 rate = bf16 dense rate x nominal 1.1 / 2.25
-                    "frac_of_tf32_tensor": (a2 / (peaks["bf16_tflops"] * 1.1 / 2.25 / 3)) if lattice else None,
+                    # algorithmic one, against the measured tcgen05 TF32 rate
+                    "frac_of_tf32_tensor": (a2 / (pk["tf32_tflops"] / 3)) if lattice else None,
                     "source": "stage timers of one fully timed solve (outside the timed region)"}
 
     # FMM apply throughput (full apply, all points sources and targets)
@@ -427,6 +472,30 @@ def run_ours(args, world, rank, local):
                 "inner_iters_total": i64.inner_iters_total, "relres_true": i64.relres_true,
                 "iters_ratio_fp32_over_fp64": info.iters / max(1, i64.iters)}
         t64.close()
+
+    # the FP32 form at scale: one solve of the 128^3 workload (k = 32, p = 8,
+    # theta = 0.35), timed like a step (L2 flushed, device time)
+    big = None
+    if not args.no_big and args.workload == WORKLOAD and args.precision == "fp32":
+        name_b = "helmholtz_n128_k32_p8"
+        wb = inputs.WORKLOADS[name_b]
+        tb0 = time.perf_counter()
+        t128 = hfmm.Tree(wb["n"], wb["k"], wb["p"], wb["theta"], wb["leaf"], "fp32")
+        torch.cuda.synchronize()
+        build_b = time.perf_counter() - tb0
+        bb = torch.from_numpy(inputs.workload_rhs(name_b)).to(dev)
+        gmb = dict(gm, restart=wb["restart"])
+        t128.gmres(bb, **gmb)          # warm-up
+        flush.fill_(1.0)
+        e0.record(stream)
+        _, ib128 = t128.gmres(bb, **gmb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        big = {"workload": name_b, "time_to_solution_s": e0.elapsed_time(e1) * 1e-3,
+               "gmres_iters": ib128.iters, "inner_iters_total": ib128.inner_iters_total,
+               "relres_true": ib128.relres_true, "converged": ib128.status == 0, "build_s": build_b}
+        t128.close()
+        del bb
 
     # BiCGSTAB with the same preconditioner (the paper's GMRES / BiCGSTAB
     # comparison).  BiCGSTAB needs a nearly fixed preconditioner: with the
@@ -563,7 +632,8 @@ def run_ours(args, world, rank, local):
             "roofline": roof, "roofline_m2l": roof_m2l, "stages_per_solve": stage_summary,
             "e2e": {"value": e2e_ms * 1e-3, "unit": "s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
-            "fp64": fp64, "bicgstab": bicg, "batched": batched, "cpu_baseline": cpu, "clocks": clk,
+            "fp64": fp64, "n128": big, "bicgstab": bicg, "batched": batched, "cpu_baseline": cpu, "clocks": clk,
+            "pipe_peaks": pk,
         }
         if dirich is not None:
             line["dirichlet"] = dirich

@@ -101,7 +101,9 @@ typedef struct hfmm_gmres_info {
 #define HFMM_STAGE_L2P     5
 #define HFMM_STAGE_P2P     6  /* near field and self term                    */
 #define HFMM_STAGE_FDM     7  /* 7-point operator inside gmres_solve         */
-#define HFMM_NSTAGES       8
+#define HFMM_STAGE_BND     8  /* boundary -> boundary apply of the inner solve
+                                 as one kernel (all its stages together)    */
+#define HFMM_NSTAGES       9
 
 typedef struct hfmm_stats {
     int L;                 /* tree depth                                   */

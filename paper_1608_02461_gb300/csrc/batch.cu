@@ -99,6 +99,13 @@ extern "C" int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_
   HFMM_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
   HFMM_CUDA_TRY(cudaEventRecord(start, s));
   const int nw = std::min(count, 8);
+  // concurrent solves keep the stage chain for their inner solves (the
+  // boundary operator's cooperative kernel wants every SM to itself)
+  std::vector<int> was_suspended(count);
+  for (int i = 0; i < count; ++i) {
+    was_suspended[i] = trees[i]->bnd_op_suspend;
+    if (nw > 1) trees[i]->bnd_op_suspend = 1;
+  }
   std::atomic<int> next{0};
   std::vector<int> status(count, HFMM_OK);
   std::vector<cudaEvent_t> done(nw, nullptr);
@@ -125,6 +132,7 @@ extern "C" int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_
   std::vector<std::thread> pool;
   for (int w = 0; w < nw; ++w) pool.emplace_back(worker, w);
   for (auto& th : pool) th.join();
+  for (int i = 0; i < count; ++i) trees[i]->bnd_op_suspend = was_suspended[i];
   int rc = HFMM_OK;
   for (int w = 0; w < nw; ++w) {
     if (done[w]) {

@@ -20,6 +20,7 @@ struct PrecGraph {
   double rtol = -1.0;
   int maxit = -1;
   int timer_mask = -1;
+  int bnd_mode = -1;            // boundary operator form captured (1: one kernel, 0: stage chain)
   int eager_its = 0;            // inner steps of the eager apply that preceded a capture
   double2* r_in = nullptr;
   double2* z_out = nullptr;
@@ -59,8 +60,63 @@ inline fmm_tree* pass_b_tree(fmm_tree* t) {
     b->timer.mask = t->timer.mask;
     b->timer.cap = t->timer.cap;
     b->skip = t->skip;
+    b->bnd_op_suspend = t->bnd_op_suspend;
   }
   return b;
+}
+
+// out = G~_{Gamma,Gamma}(scale in) + self term on the boundary points (the
+// operator of the inner solve): one persistent kernel when the tree has a
+// plan for it (built on first use, outside any capture), else the stage chain
+static bool bnd_op_usable(fmm_tree* t, cudaStream_t s) {
+  // not inside gmres_solve_batched: concurrent solves would run several
+  // cooperative kernels at once, each waiting for all of its CTAs
+  if (!t->use_bnd_op || t->bnd_op_suspend || t->n_bnd == 0) return false;
+  if (!t->bop) {  // the plan is built outside any stream capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return false;
+  }
+  return bnd_op_ready(t, s) == HFMM_OK;
+}
+
+// the inner solve V q = -g as one GMRES cycle inside the boundary operator's
+// kernel: when the tree has the plan, the solve is one cycle (inner_m >=
+// inner_maxit) and the cycle fits the kernel (at most 128 steps)
+static bool bnd_cycle_usable(fmm_tree* tb, int inner_m, int inner_maxit, cudaStream_t s) {
+  if (inner_m < inner_maxit || !bnd_op_usable(tb, s)) return false;
+  if (!bnd_op_cycle_planned(tb, inner_maxit)) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return false;
+    if (bnd_op_cycle_ready(tb, inner_maxit, s) != HFMM_OK) return false;
+  }
+  return true;
+}
+
+// form of the inner solve's operator that a captured graph would hold
+static int bnd_mode_of(fmm_tree* t) {
+  const fmm_tree* b = t->inner ? t->inner : t;
+  return (b->use_bnd_op && !t->bnd_op_suspend && bnd_op_planned(b)) ? 1 : 0;
+}
+
+template <typename V>
+static int bnd_apply(fmm_tree* tb, const V* in, V* out, double scale, cudaStream_t s) {
+  if (bnd_op_usable(tb, s)) {
+    tb->timer.begin(HFMM_STAGE_BND, s);
+    const int st = fmm_bnd_apply(tb, in, out, scale, s);
+    tb->timer.end(1, s);
+    return st;
+  }
+  HFMM_TRY(fmm_gather(tb, HFMM_SET_BND, nullptr, 0.0, in, scale, s));
+  HFMM_TRY(fmm_core(tb, HFMM_SET_BND, HFMM_SET_BND, s));
+  return fmm_scatter(tb, HFMM_SET_BND, nullptr, out, s);
 }
 
 static void prec_graph_drop(PrecGraph& G) {
@@ -104,6 +160,7 @@ void release(fmm_tree* t) {
   t->near_stream = nullptr;
   t->timer.destroy();
   m2l_tc_release(t);
+  bnd_op_release(t);
   if (t->gaunt) cudaFree(t->gaunt);
   t->gaunt = nullptr;
 }
@@ -184,6 +241,7 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   if (const char* v = getenv("HFMM_BASIS_TABLE")) t->use_rtab = atoi(v) != 0;
   if (const char* v = getenv("HFMM_OVERLAP_NEAR")) t->overlap_near = atoi(v) != 0;
   if (const char* v = getenv("HFMM_M2L_TC")) t->use_m2l_tcore = atoi(v);
+  if (const char* v = getenv("HFMM_BND_OP")) t->use_bnd_op = atoi(v) != 0;
   HFMM_TRY(tree_alloc(t, &t->m2l_part, csz * t->total_cells * P * t->m2l_part_max));
   HFMM_TRY(tree_alloc_t(t, &t->g_bnd, t->n_bnd + 1));
   HFMM_TRY(tree_alloc_t(t, &t->q_bnd, t->n_bnd + 1));
@@ -313,6 +371,13 @@ extern "C" int fmm_apply(fmm_tree* t, int src_set, int tgt_set, const void* d_q_
   if ((out_set & HFMM_SET_BND) && t->n_bnd > 0 && !d_phi_bnd) return HFMM_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   HFMM_CUDA_TRY(cudaEventRecord(t->ev0, s));
+  if (mode == HFMM_FWD && src_set == HFMM_SET_BND && tgt_set == HFMM_SET_BND && bnd_op_usable(t, s)) {
+    t->timer.begin(HFMM_STAGE_BND, s);
+    HFMM_TRY(fmm_bnd_apply(t, (const double2*)d_q_bnd, (double2*)d_phi_bnd, 1.0, s));
+    t->timer.end(1, s);
+    HFMM_CUDA_TRY(cudaEventRecord(t->ev1, s));
+    return HFMM_OK;
+  }
   HFMM_TRY(fmm_gather(t, in_set, (const double2*)d_q_vol, 1.0, (const double2*)d_q_bnd, 1.0, s));
   if (mode == HFMM_FWD) {
     HFMM_TRY(fmm_core(t, src_set, tgt_set, s));
@@ -393,6 +458,32 @@ extern "C" int hfmm_dirichlet_rhs(fmm_tree* t, const void* d_f, const void* d_u_
   return hfmm_last_launch();
 }
 
+// the inner boundary solve (-V) q = g (Sec. 5.2, Eq. (ubound); reading B4:
+// GMRES from q = 0 to inner_rtol, at most inner_maxit steps, restart
+// inner_m), V x = h^2 G_{Gamma,Gamma} x + s_Gamma x: one cycle inside the
+// boundary operator's kernel when that applies, else the stage-by-stage
+// GMRES; *inner_iters gets the steps taken (a host read)
+template <typename R>
+static int inner_solve(fmm_tree* t, fmm_tree* tb, GmresWorkT<R>& W, const C<R>* g, C<R>* q, double h2,
+                       double inner_rtol, int inner_maxit, int inner_m, int* inner_iters, cudaStream_t s) {
+  if (bnd_cycle_usable(tb, inner_m, inner_maxit, s)) {
+    tb->timer.begin(HFMM_STAGE_BND, s);
+    HFMM_TRY(fmm_bnd_cycle(tb, g, q, -h2, inner_maxit, inner_rtol, nullptr, s));
+    tb->timer.end(1, s);
+    int its = 0;
+    HFMM_CUDA_TRY(cudaMemcpyAsync(&its, bnd_op_cycle_flags(tb) + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (inner_iters) *inner_iters = its;
+    return HFMM_OK;
+  }
+  DevOpT<R> negV = [tb, h2, s](const C<R>* in, C<R>* out) -> int { return bnd_apply(tb, in, out, -h2, s); };
+  HFMM_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(C<R>) * t->n_bnd, s));
+  GmresResult ir;
+  HFMM_TRY(gmres_run<R>(W, negV, nullptr, g, q, inner_m, inner_rtol, inner_maxit, true, false, &ir, nullptr, 0, s));
+  if (inner_iters) *inner_iters = ir.iters;
+  return HFMM_OK;
+}
+
 // z = M^-1 r (Sec. 5.2-5.3, homogeneous Dirichlet data).  The inner solve
 // runs on complex vectors of real type R: the precision of the FMM form.
 template <typename R>
@@ -412,15 +503,7 @@ static int precond_impl_t(fmm_tree* t, const double2* r, double2* z, double inne
   // written as (-V) q = g
   HFMM_TRY(gmres_work_reserve(W, t->n_bnd, inner_m, false));
   fmm_tree* tb = pass_b_tree(t);
-  DevOpT<R> negV = [tb, h2, s](const C<R>* in, C<R>* out) -> int {
-    HFMM_TRY(fmm_gather(tb, HFMM_SET_BND, nullptr, 0.0, in, -h2, s));
-    HFMM_TRY(fmm_core(tb, HFMM_SET_BND, HFMM_SET_BND, s));
-    return fmm_scatter(tb, HFMM_SET_BND, nullptr, out, s);
-  };
-  HFMM_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(C<R>) * t->n_bnd, s));
-  GmresResult ir;
-  HFMM_TRY(gmres_run<R>(W, negV, nullptr, g, q, inner_m, inner_rtol, inner_maxit, true, false, &ir, nullptr, 0, s));
-  if (inner_iters) *inner_iters = ir.iters;
+  HFMM_TRY(inner_solve<R>(t, tb, W, g, q, h2, inner_rtol, inner_maxit, inner_m, inner_iters, s));
   // Pass C: z = G_{Omega,Omega} (h^3 r) + G_{Omega,Gamma} (h^2 q) + s_Omega r
   HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, r, h3, q, h2, s));
   HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, s));
@@ -460,15 +543,7 @@ static int bem_dirichlet_impl_t(fmm_tree* t, const double2* f, const double2* ub
   // (-V) q = g
   HFMM_TRY(gmres_work_reserve(W, t->n_bnd, inner_m, false));
   fmm_tree* tb = pass_b_tree(t);
-  DevOpT<R> negV = [tb, h2, s](const C<R>* in, C<R>* out) -> int {
-    HFMM_TRY(fmm_gather(tb, HFMM_SET_BND, nullptr, 0.0, in, -h2, s));
-    HFMM_TRY(fmm_core(tb, HFMM_SET_BND, HFMM_SET_BND, s));
-    return fmm_scatter(tb, HFMM_SET_BND, nullptr, out, s);
-  };
-  HFMM_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(C<R>) * t->n_bnd, s));
-  GmresResult ir;
-  HFMM_TRY(gmres_run<R>(W, negV, nullptr, g, q, inner_m, inner_rtol, inner_maxit, true, false, &ir, nullptr, 0, s));
-  if (inner_iters) *inner_iters = ir.iters;
+  HFMM_TRY(inner_solve<R>(t, tb, W, g, q, h2, inner_rtol, inner_maxit, inner_m, inner_iters, s));
   // u = N_{Omega,Omega} f + V_{Omega,Gamma} q + s_Omega f - D_{Omega,Gamma} u_Gamma
   HFMM_TRY(fmm_gather(t, HFMM_SET_VOL | HFMM_SET_BND, f, h3, q, h2, s));
   HFMM_TRY(fmm_core(t, HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL, s));
@@ -506,12 +581,15 @@ static int prec_graph_body_t(fmm_tree* t, double rtol, int maxit, cudaStream_t c
   HFMM_TRY(fmm_scatter(t, HFMM_SET_BND, nullptr, g, c));
   t->skip = G.flags;
   fmm_tree* tb = pass_b_tree(t);
-  DevOpT<R> negV = [tb, h2, c](const C<R>* in, C<R>* out) -> int {
-    HFMM_TRY(fmm_gather(tb, HFMM_SET_BND, nullptr, 0.0, in, -h2, c));
-    HFMM_TRY(fmm_core(tb, HFMM_SET_BND, HFMM_SET_BND, c));
-    return fmm_scatter(tb, HFMM_SET_BND, nullptr, out, c);
-  };
-  int st = gmres_cycle_device<R>(W, negV, g, q, maxit, rtol, G.flags, G.flags + 1, G.flags + 2, c);
+  int st;
+  if (bnd_cycle_usable(tb, maxit, maxit, c)) {  // one cycle inside the boundary operator's kernel
+    tb->timer.begin(HFMM_STAGE_BND, c);
+    st = fmm_bnd_cycle(tb, g, q, -h2, maxit, rtol, G.flags, c);
+    tb->timer.end(1, c);
+  } else {
+    DevOpT<R> negV = [tb, h2, c](const C<R>* in, C<R>* out) -> int { return bnd_apply(tb, in, out, -h2, c); };
+    st = gmres_cycle_device<R>(W, negV, g, q, maxit, rtol, G.flags, G.flags + 1, G.flags + 2, c);
+  }
   t->skip = nullptr;
   if (tb != t) {
     tb->skip = nullptr;
@@ -572,6 +650,7 @@ static int prec_graph_build(fmm_tree* t, const double2* r, double2* z, double rt
   G.rtol = rtol;
   G.maxit = maxit;
   G.timer_mask = t->timer.on ? t->timer.mask : 0;
+  G.bnd_mode = bnd_mode_of(t);
   return HFMM_OK;
 }
 
@@ -584,7 +663,7 @@ static int precond_graph(fmm_tree* t, const double2* r, double2* z, double rtol,
     t->timer.resolve_slots(G.slots);
     G.pending = false;
   }
-  if (!G.exec || G.rtol != rtol || G.maxit != maxit || G.timer_mask != tmask)
+  if (!G.exec || G.rtol != rtol || G.maxit != maxit || G.timer_mask != tmask || G.bnd_mode != bnd_mode_of(t))
     HFMM_TRY(prec_graph_build(t, r, z, rtol, maxit, s));
   HFMM_CUDA_TRY(cudaMemcpyAsync(G.r_in, r, sizeof(double2) * t->n_vol, cudaMemcpyDeviceToDevice, s));
   HFMM_CUDA_TRY(cudaGraphLaunch(G.exec, s));

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <utility>
 
+#include "m2l_product.cuh"
 #include "special.cuh"
 #include "tree.cuh"
 
@@ -724,59 +725,6 @@ __global__ void k_m2l_valid(const int4* __restrict__ tiles, const int* __restric
         ++n;
       }
     nval[blockIdx.x] = n;
-  }
-}
-
-// RT row groups x 8 column groups of threads; a thread owns rows r0 + r RT
-// (r < R) and columns c0 + j 8 (j < CM) of the P x TC output tile.
-// acc[r][j] += sum_a T(r0 + r RT, a) M(c0 + 8 j, a) for one staged offset:
-// T row-major (P x P), source rows of stride MS; two consecutive a per step
-// read with one 16-byte load per row (FP32) or two (FP64).  P is even.
-template <typename T, int R, int CM, int RT>
-__device__ __forceinline__ void m2l_block_product(const C<T>* __restrict__ Ts, const C<T>* __restrict__ Ms,
-                                                  int P, int MS, int r0, int c0, C<T> (&acc)[R][CM]) {
-  constexpr int CT = 8;
-  const C<T>* trow[R];
-  const C<T>* mrow[CM];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    int ap = r0 + r * RT;
-    trow[r] = Ts + (size_t)(ap < P ? ap : 0) * P;
-  }
-#pragma unroll
-  for (int j = 0; j < CM; ++j) mrow[j] = Ms + (size_t)(c0 + j * CT) * MS;
-#pragma unroll 2
-  for (int a = 0; a < P; a += 2) {
-    C<T> t0[R], t1[R], m0[CM], m1[CM];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if constexpr (sizeof(T) == 4) {
-        float4 v = *reinterpret_cast<const float4*>(trow[r] + a);
-        t0[r] = mkc<T>(v.x, v.y);
-        t1[r] = mkc<T>(v.z, v.w);
-      } else {
-        t0[r] = trow[r][a];
-        t1[r] = trow[r][a + 1];
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < CM; ++j) {
-      if constexpr (sizeof(T) == 4) {
-        float4 v = *reinterpret_cast<const float4*>(mrow[j] + a);
-        m0[j] = mkc<T>(v.x, v.y);
-        m1[j] = mkc<T>(v.z, v.w);
-      } else {
-        m0[j] = mrow[j][a];
-        m1[j] = mrow[j][a + 1];
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int j = 0; j < CM; ++j) {
-        cfma<T>(acc[r][j], t0[r], m0[j]);
-        cfma<T>(acc[r][j], t1[r], m1[j]);
-      }
   }
 }
 
@@ -2753,10 +2701,16 @@ int fmm_device_error(cudaStream_t s, bool clear) {
     HFMM_CUDA_TRY(cudaMemcpyToSymbolAsync(g_fmm_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
   }
   if (m2l_tc_error(s, clear)) h = HFMM_ERR_TIMEOUT;
+  if (bnd_op_error(s, clear)) h = HFMM_ERR_TIMEOUT;
   return h;
 }
 
 int set_smem_any(const void* fn, size_t bytes) { return set_smem<float>(fn, bytes); }
+
+int fmm_pair_lists(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
+  const size_t csz = t->precision == HFMM_FP32 ? sizeof(float2) : sizeof(double2);
+  return m2l_pair_lists(t, src_set, tgt_set, csz, s);
+}
 
 int fmm_core(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
   if (t->precision == HFMM_FP32) return core_impl<float>(t, src_set, tgt_set, s);

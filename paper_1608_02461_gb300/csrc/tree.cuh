@@ -14,6 +14,7 @@ struct DevBuf {
 
 struct fmm_tree_ext;  // solver workspaces (capi.cu)
 struct fmm_tc_state;  // tensor-core M2L state (m2l_tc.cu)
+struct bnd_op_state;  // boundary -> boundary apply as one kernel (bnd_op.cu)
 
 // kernels launched by the library (all handles)
 void count_launches(int64_t n);
@@ -265,6 +266,12 @@ struct fmm_tree {
   void* qs = nullptr;           // [n_pts] sorted weights
   void* phis = nullptr;         // [n_pts] sorted potentials
 
+  // ---- boundary -> boundary apply of the inner solve as one persistent
+  //      kernel (plan built on first use); use_bnd_op 0: the stage chain
+  bnd_op_state* bop = nullptr;
+  int use_bnd_op = 1;
+  int bnd_op_suspend = 0;       // set while the handle runs inside gmres_solve_batched
+
   int use_graphs = 1;           // gmres_solve replays the preconditioner as one CUDA graph
   // auxiliary tree over the same points with expansion order inner_p, used
   // for the boundary -> boundary applies of the preconditioner's inner solve
@@ -349,6 +356,31 @@ int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cu
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, float2* phi_bnd, cudaStream_t s);
 int fmm_scatter_from(fmm_tree* t, const void* sorted, int tgt_set, double2* phi_vol, double2* phi_bnd,
                      cudaStream_t s);
+
+// bnd_op.cu: y = G~(scale x) between the boundary points (x, y in the original
+// boundary order) as one cooperative kernel; HFMM_ERR_UNSUPPORTED when the
+// tree does not qualify (the caller then runs the stage chain).  The first
+// call builds the plan (host synchronisation: not inside a stream capture).
+int fmm_bnd_apply(fmm_tree* t, const float2* x, float2* y, double scale, cudaStream_t s);
+int fmm_bnd_apply(fmm_tree* t, const double2* x, double2* y, double scale, cudaStream_t s);
+int bnd_op_ready(fmm_tree* t, cudaStream_t s);  // builds the plan; HFMM_OK when usable
+bool bnd_op_planned(const fmm_tree* t);          // a usable plan exists
+// one GMRES cycle of m <= 128 steps from x = 0 for (G~ scale) x = b between the
+// boundary points (b, x in the original order), inside the same kernel; the
+// flags (device, or the plan's own when null): [0] done, [1] steps,
+// [2] += steps.  bnd_op_cycle_ready builds the plan and the workspace (not
+// inside a capture).
+int bnd_op_cycle_ready(fmm_tree* t, int m, cudaStream_t s);
+int fmm_bnd_cycle(fmm_tree* t, const float2* b, float2* x, double scale, int m, double rtol, int* d_flags,
+                  cudaStream_t s);
+int fmm_bnd_cycle(fmm_tree* t, const double2* b, double2* x, double scale, int m, double rtol, int* d_flags,
+                  cudaStream_t s);
+const int* bnd_op_cycle_flags(const fmm_tree* t);
+bool bnd_op_cycle_planned(const fmm_tree* t, int m);
+int bnd_op_error(cudaStream_t s, bool clear);
+void bnd_op_release(fmm_tree* t);
+// fmm.cu: pair lists of a (source set, target set) pass, built on first use
+int fmm_pair_lists(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
 
 // krylov.cu
 int fdm_apply_dev(int n, double h, double k, const double2* u, double2* out, cudaStream_t s);

@@ -50,8 +50,8 @@ class hfmm_gmres_info(ctypes.Structure):
                 ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int)]
 
 
-NSTAGES = 8
-STAGES = ["gather", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "fdm"]
+NSTAGES = 9
+STAGES = ["gather", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "fdm", "bnd"]
 
 
 class hfmm_stats(ctypes.Structure):

@@ -1,0 +1,119 @@
+"""The boundary -> boundary FMM apply as one persistent kernel (the operator
+of the preconditioner's inner solve, Sec. 5.2-5.3, every FMM stage of
+Sec. 5.1.2 as a phase of one launch): against the oracle's FMM in FP64
+(1e-11 relative L2) on trees of depth 2, 3 and 4, against the stage chain it
+replaces (FP64 1e-13 and FP32 2e-6, depth 4 and the depth-5 128^3 tree),
+deterministic, and inside the preconditioned solve (same iterations as the
+stage chain within one, graph replay equal to the host-driven form)."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bem  # noqa: E402
+from paper_1608_02461_gb300 import hfmm, inputs  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def tree(n, k, p, theta, leaf, prec, bnd_op=True):
+    old = os.environ.get("HFMM_BND_OP")
+    os.environ["HFMM_BND_OP"] = "1" if bnd_op else "0"
+    try:
+        return hfmm.Tree(n, k, p, theta, leaf, prec)
+    finally:
+        if old is None:
+            os.environ.pop("HFMM_BND_OP", None)
+        else:
+            os.environ["HFMM_BND_OP"] = old
+
+
+def bnd_apply(t, qb):
+    _, pb = t.apply(None, torch.from_numpy(qb).to(DEV), src=hfmm.SET_BND, tgt=hfmm.SET_BND)
+    torch.cuda.synchronize()
+    return pb.cpu().numpy()
+
+
+def uses_kernel(t):
+    """The apply went through the one-kernel form (its stage timer ran)."""
+    t.set_timing(True, stages=["bnd"])
+    bnd_apply(t, inputs.complex_normal(t.n_bnd, 9))
+    used = t.stage_times()["bnd"][1] > 0
+    t.set_timing(False)
+    return used
+
+
+@pytest.mark.parametrize("case", [(7, 3.0, 4, 32, 0.4),     # L = 2
+                                  (12, 9.0, 6, 16, 0.35),   # L = 3
+                                  (13, 25.0, 4, 16, 0.4),   # L = 3, high k
+                                  (20, 6.0, 6, 8, 0.4),     # L = 4
+                                  (18, 11.0, 8, 8, 0.35)])  # L = 4, p = 8
+def test_bnd_op_fp64_matches_oracle(case):
+    n, k, p, leaf, theta = case
+    t = tree(n, k, p, theta, leaf, "fp64")
+    assert uses_kernel(t)
+    pr = bem.Problem(n, k, p, leaf, theta)
+    assert t.stats().L == pr.fmm.L
+    qb = inputs.complex_normal(pr.NG, 800 + n)
+    q = np.concatenate([np.zeros(pr.NO, dtype=np.complex128), qb])
+    ref = pr.fmm.apply(q, pr.bnd, pr.bnd, pr.sigma)[pr.bnd]
+    got = bnd_apply(t, qb)
+    assert rel(got, ref) < 1e-11, rel(got, ref)
+    again = bnd_apply(t, qb)
+    assert np.array_equal(got, again)
+    t.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+@pytest.mark.parametrize("case", [(64, 16.0, 6, 64, 0.4), (128, 32.0, 8, 64, 0.35)])
+def test_bnd_op_matches_stage_chain(case, prec, tol):
+    n, k, p, leaf, theta = case
+    if prec == "fp64" and n > 64:
+        pytest.skip("FP64 at 128^3 is covered at depth 4")
+    a = tree(n, k, p, theta, leaf, prec, bnd_op=True)
+    b = tree(n, k, p, theta, leaf, prec, bnd_op=False)
+    assert uses_kernel(a) and not uses_kernel(b)
+    qb = inputs.complex_normal(6 * n * n, 810)
+    ga, gb = bnd_apply(a, qb), bnd_apply(b, qb)
+    assert rel(ga, gb) < tol, rel(ga, gb)
+    a.close()
+    b.close()
+
+
+def test_bnd_op_solve_matches_stage_chain():
+    """The FP32 solve of the 64^3 workload with the inner solve on the one-
+    kernel operator: converged to 1e-6 in the stage chain's iterations +-1."""
+    name = "helmholtz_n64_k16_p6"
+    w = inputs.WORKLOADS[name]
+    b = torch.from_numpy(inputs.workload_rhs(name)).to(DEV)
+    kw = dict(restart=w["restart"], rtol=1e-6, inner_rtol=1e-2, inner_maxit=20, inner_m=20)
+    ta = tree(w["n"], w["k"], w["p"], w["theta"], w["leaf"], "fp32", bnd_op=True)
+    tb = tree(w["n"], w["k"], w["p"], w["theta"], w["leaf"], "fp32", bnd_op=False)
+    xa, ia = ta.gmres(b, **kw)
+    xb, ib = tb.gmres(b, **kw)
+    assert ia.status == 0 and ia.relres_true < 1e-6
+    assert abs(ia.iters - ib.iters) <= 1, (ia.iters, ib.iters)
+    xa2, ia2 = ta.gmres(b, **kw)  # graph replay: deterministic
+    assert ia2.iters == ia.iters and torch.equal(xa, xa2)
+    ta.close()
+    tb.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bnd_op_graph_equals_host_driven(prec):
+    n = 16
+    t = tree(n, 9.0, 6, 0.4, 8, prec)
+    rhs = torch.from_numpy(inputs.rhs("uniform_real", n, 73)).to(DEV)
+    kw = dict(restart=30, rtol=1e-6, inner_rtol=1e-2, inner_maxit=20, inner_m=20)
+    x1, i1 = t.gmres(rhs, **kw)
+    t.use_graphs(False)
+    x2, i2 = t.gmres(rhs, **kw)
+    assert i1.iters == i2.iters and torch.equal(x1, x2)
+    t.close()

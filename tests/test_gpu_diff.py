@@ -163,7 +163,12 @@ def test_gradient_through_the_solve():
         fd = (loss(tree, b + h * d) - loss(tree, b - h * d)) / (2 * h)
         an = torch.real(torch.vdot(bb.grad, d)).item()
         assert abs(fd - an) <= 1e-6 * abs(an) + 1e-9, (s, fd, an)
-    tp = hfmm.Tree(n, k + h, p, 0.4, 8, "fp64")
-    tm = hfmm.Tree(n, k - h, p, 0.4, 8, "fp64")
-    fdk = (loss(tp, b) - loss(tm, b)) / (2 * h)
+    # in k a larger step: the loss (about n^3) carries a rounding of about
+    # 2e-16 n^3, which a difference over 2h = 2e-6 would turn into 1e-8, a
+    # few 1e-6 of dL/dk here; with h = 1e-4 rounding gives 1e-10 and the
+    # O(h^2) truncation about 1e-8 relative
+    hk = 1e-4
+    tp = hfmm.Tree(n, k + hk, p, 0.4, 8, "fp64")
+    tm = hfmm.Tree(n, k - hk, p, 0.4, 8, "fp64")
+    fdk = (loss(tp, b) - loss(tm, b)) / (2 * hk)
     assert abs(fdk - gk) <= 1e-6 * abs(gk), (fdk, gk)
