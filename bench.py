@@ -570,8 +570,9 @@ def run_ours(args, world, rank, local):
     batched = None
     if not args.no_batched:
         probs = inputs.batched_problems()
+        orders = [hfmm.order_for_k(q["k"], q["p"]) for q in probs]
         tb0 = time.perf_counter()
-        trees = [hfmm.Tree(q["n"], q["k"], q["p"], q["theta"], q["leaf"], "fp32") for q in probs]
+        trees = [hfmm.Tree(q["n"], q["k"], p_, q["theta"], q["leaf"], "fp32") for q, p_ in zip(probs, orders)]
         for tr in trees:
             tr.autotune()
         torch.cuda.synchronize()
@@ -599,8 +600,10 @@ def run_ours(args, world, rank, local):
         batched = {"solves": len(probs), "converged": int(sum(conv)), "maxit": args.batched_maxit,
                    "batched_s": tbat, "sequential_s": tseq, "speedup": tseq / tbat,
                    "setup_s": setup_s, "gmres_iters": [i.iters for i in binfos],
-                   "unconverged": [dict(n=q["n"], k=round(q["k"], 3), p=q["p"])
-                                   for q, c in zip(probs, conv) if not c]}
+                   "order_rule": "hfmm_order_for_k(k, p requested)",
+                   "orders_raised": sum(1 for q, p_ in zip(probs, orders) if p_ != q["p"]),
+                   "unconverged": [dict(n=q["n"], k=round(q["k"], 3), p=p_)
+                                   for q, p_, c in zip(probs, orders, conv) if not c]}
         for tr in trees:
             tr.close()
 

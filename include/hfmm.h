@@ -278,6 +278,49 @@ int hfmm_dirichlet_rhs(fmm_tree* tree, const void* d_f, const void* d_u_bnd, voi
 int hfmm_fdm_apply(fmm_tree* tree, const void* d_u, void* d_out, void* stream);
 
 /*
+ * hfmm_order_for_k -- the expansion order to build a lattice tree with for
+ * wavenumber k when at least p_min is asked for (host function, no device
+ * work).  A multipole or local expansion of order p (degrees below p) of a
+ * cell of half-diagonal rho resolves e^{ikr}/r only for p above about
+ * k rho (the spherical Bessel functions j_n(k rho) become small for
+ * n > k rho; Sec. 5.1.2 expansions).  The coarsest level with M2L
+ * interactions is level 2 of the unit cube, rho_2 = sqrt(3)/8, so the
+ * order is the smallest even p >= max(p_min, ceil(k rho_2) + 1).  With a
+ * fixed order the preconditioner degrades as k grows (GMRES iterations rise
+ * and at p = 4, k > 21 the solve stalls); with this order the iteration
+ * count stays near that of moderate k.
+ * Returns the order (>= 1), or INVALID_ARG (k < 0 or not finite, p_min
+ * outside 1..16) or UNSUPPORTED (the rule asks for more than order 16).
+ */
+int hfmm_order_for_k(double k, int p_min);
+
+/*
+ * fmm_grad_k -- the wavenumber gradient of a real loss of phi = G~ q on the
+ * volume points (fmm_apply VOL -> VOL, HFMM_FWD):
+ *   *d_out = Re sum_i conj(g_i) (dG~/dk q)_i,   g = dL/dphi
+ * (PyTorch's convention for complex tensors).  The tangent apply (HFMM_DK)
+ * writes into device memory held by the handle (n_vol complex128, allocated
+ * on the first call); the sum runs on the device in FP64 in a fixed order
+ * (bit-identical on repeated calls).
+ *   d_q_vol, d_g_vol  n_vol complex128 (device), read only
+ *   d_out             one double (device), overwritten
+ * Errors: INVALID_ARG (null pointer, no volume points), NOMEM, CUDA.
+ */
+int fmm_grad_k(fmm_tree* tree, const void* d_q_vol, const void* d_g_vol, double* d_out, void* stream);
+
+/*
+ * hfmm_solve_grad_k -- the wavenumber gradient of a real loss of the solution
+ * x = A(k)^-1 b of the 7-point system (Sec. 2).  For real k, A is real and
+ * symmetric with dA/dk = -2k I, so with lam the solution of A lam = dL/dx:
+ *   *d_out = -Re <lam, (dA/dk) x> = 2k Re sum_i conj(lam_i) x_i
+ * summed on the device in FP64 in a fixed order.
+ *   d_lam, d_x  n^3 complex128 (device), read only
+ *   d_out       one double (device), overwritten
+ * Lattice trees only (UNSUPPORTED otherwise).  Errors: INVALID_ARG, NOMEM, CUDA.
+ */
+int hfmm_solve_grad_k(fmm_tree* tree, const void* d_lam, const void* d_x, double* d_out, void* stream);
+
+/*
  * gmres_solve -- Sec. 3-4, Sec. 6: flexible right-preconditioned restarted
  * GMRES(m) for A x = b with A the 7-point operator of the tree's (n, k) and
  * M^-1 = fmm_precond_apply.  Classical Gram-Schmidt with reorthogonalisation,
@@ -332,12 +375,16 @@ int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_x, int coun
 
 /*
  * fmm_autotune -- times the M2L kernel variants (two-stage block pipeline,
- * warp-specialised three-stage pipeline) and the split of the per-tile
- * offset lists (grid filled to 1, 2, 4 or 8 x 152 blocks) on the FMM passes
- * of the preconditioner and on the full apply, and keeps the fastest per pass
- * in the handle.  The choice changes only the order in which far-field
- * contributions are summed (rounding-level differences); a handle's results
- * stay deterministic.
+ * warp-specialised three-stage pipeline, pair lists) and the split of the
+ * per-tile offset lists (grid filled to 1, 2, 4 or 8 x 152 blocks) on the
+ * FMM passes of the preconditioner and on the full apply, then, with the
+ * chosen M2L, the tile shapes of the lattice near field (tiled 4 x 4
+ * target-source groups or not in the FP32 form; at most 8, 16 or 32 threads
+ * per group of targets; one block per SM or as many as fit), and keeps the
+ * fastest per pass in the handle.  The choice changes only the order in
+ * which contributions are summed (rounding-level differences); a handle's
+ * results stay deterministic.  Also tunes the handle's inner-order tree
+ * (fmm_set_inner_order) when it has one.
  */
 int fmm_autotune(fmm_tree* tree, void* stream);
 

@@ -10,7 +10,10 @@
 // fmm_autotune times the M2L kernel variants (two-stage block pipeline,
 // warp-specialised three-stage pipeline, pair lists) and the split of the offset lists
 // (grid filled to 1, 2, 4 or 8 times the SM count) on the FMM passes the
-// preconditioner uses, and keeps the fastest per pass in the handle.
+// preconditioner uses, then, with that M2L, the shapes of the lattice near
+// field (tiled 4 x 4 target-source groups or not, at most 8, 16 or 32
+// threads per target group, one block per SM or as many as fit), and keeps
+// the fastest per pass in the handle.
 #include <algorithm>
 #include <atomic>
 #include <thread>
@@ -77,6 +80,35 @@ extern "C" int fmm_autotune(fmm_tree* t, void* stream) {
       }
     t->tuned_variant[ci] = bv;
     t->tuned_fill[ci] = bf;
+    // near-field shapes (lattice trees whose near field goes through the table)
+    const bool lat = t->lat_D > 0 && t->use_lattice_p2p && t->near_count <= 128 &&
+                     (t->precision == HFMM_FP32 || t->lat_tab64_fits);
+    if (!lat) continue;
+    best = 1e30f;
+    int btile = 0, btpt = 32, bblk = 0;
+    const int ntile = t->precision == HFMM_FP32 ? 2 : 1;
+    for (int tile = 0; tile < ntile; ++tile)
+      for (int tpt : {8, 16, 32})
+        for (int blk : {1, 0}) {
+          t->tuned_p2p_tile[ci] = tile;
+          t->tuned_p2p_tpt[ci] = tpt;
+          t->tuned_p2p_blocks[ci] = blk;
+          float ms = 0.f;
+          int st = time_core(t, src, tgt, s, 3, &ms);
+          if (st != HFMM_OK) {
+            t->timer.on = timer_was_on;
+            return st;
+          }
+          if (ms < best) {
+            best = ms;
+            btile = tile;
+            btpt = tpt;
+            bblk = blk;
+          }
+        }
+    t->tuned_p2p_tile[ci] = btile;
+    t->tuned_p2p_tpt[ci] = btpt;
+    t->tuned_p2p_blocks[ci] = bblk;
   }
   t->timer.on = timer_was_on;
   if (t->inner) return fmm_autotune(t->inner, stream);  // the inner solve's tree

@@ -41,17 +41,23 @@ constexpr int DOWN_ROWS_PRE = 1, DOWN_NEAR_PRE = 2;
 constexpr int BO_MAX_PH = 12, BO_MAX_SEG = 4, BO_MAX_NG = 5;
 constexpr int BO_CHUNK = 32;  // pairs per product item (the pair lists' chunk size)
 
-// product groups per CTA of a configuration (R rows of RT groups per thread):
-// as many as the shared memory holds, at most BO_MAX_NG and 512 threads; the
-// launch bound follows, so that the smaller CTAs keep more registers
-__host__ __device__ constexpr int bo_groups(int R, int RT, int csz) {
+// product groups per CTA of a configuration (R rows of RT groups per thread)
+// and copy stages per group: two stages when at least four groups fit the
+// shared memory that way, else one stage with as many groups as fit; at most
+// BO_MAX_NG groups and 512 threads.  The launch bound follows, so that the
+// smaller CTAs keep more registers.
+__host__ __device__ constexpr int bo_fit(int R, int RT, int csz, int nst) {
   const int P = R * RT;  // largest P of the configuration
-  const int gbytes = 2 * (P * P + 32 * (P + 2)) * csz;
+  const int gbytes = nst * (P * P + 32 * (P + 2)) * csz;
   const int by_smem = (200 * 1024) / gbytes;
   const int by_thr = 512 / (RT * 8);
   const int n = by_smem < by_thr ? by_smem : by_thr;
   return n < BO_MAX_NG ? (n < 1 ? 1 : n) : BO_MAX_NG;
 }
+__host__ __device__ constexpr int bo_stages(int R, int RT, int csz) {
+  return (bo_fit(R, RT, csz, 2) >= 4 || bo_fit(R, RT, csz, 2) == bo_fit(R, RT, csz, 1)) ? 2 : 1;
+}
+__host__ __device__ constexpr int bo_groups(int R, int RT, int csz) { return bo_fit(R, RT, csz, bo_stages(R, RT, csz)); }
 
 struct BoSeg {
   int type, level, first, count;
@@ -71,6 +77,7 @@ struct BoArgs {
   T scale;           // weights q = scale x
   const int* skip;   // when set and nonzero the kernel returns at once
   int P, L, nb, ng;  // coefficients, leaf level, boundary points, thread groups per CTA
+  int nst;           // copy stages per product group (1 or 2)
   T k;
   C<T> sig;          // self coefficient per unit weight
   // boundary points in sorted (leaf-Morton) order
@@ -635,10 +642,11 @@ __device__ bool bo_products(const BoArgs<T, IO>& A, const BoSeg& sg, unsigned ch
   const int g = threadIdx.x / GT, tg = threadIdx.x - g * GT;
   if (g >= A.ng) return true;
   const size_t op_elems = (size_t)P * P, ms_elems = (size_t)TC * MS;
-  C<T>* base = reinterpret_cast<C<T>*>(sm) + (size_t)g * 2 * (op_elems + ms_elems);
+  const int NST = A.nst;
+  C<T>* base = reinterpret_cast<C<T>*>(sm) + (size_t)g * NST * (op_elems + ms_elems);
   C<T>* Ts0 = base;
   C<T>* Ms0 = base + op_elems;
-  C<T>* Ts1 = base + op_elems + ms_elems;
+  C<T>* Ts1 = base + op_elems + ms_elems;  // second stage (NST == 2)
   C<T>* Ms1 = Ts1 + op_elems;
   uint64_t* bar = mbar + 2 * g;
   const int gid = blockIdx.x * A.ng + g, ngt = gridDim.x * A.ng;
@@ -693,16 +701,19 @@ __device__ bool bo_products(const BoArgs<T, IO>& A, const BoSeg& sg, unsigned ch
   {
     Pre p0, p1;
     preload(0, p0);
-    preload(1, p1);
+    if (NST == 2) preload(1, p1);
     issue(0, p0);
-    issue(1, p1);
+    if (NST == 2) issue(1, p1);
   }
   bool ok = true;
   for (int j = 0; sg.first + gid + j * ngt < end; ++j) {
-    const int st = j & 1;
+    const int st = NST == 2 ? (j & 1) : 0;
     Pre pn;
-    preload(j + 2, pn);
-    cp_async_wait1();
+    preload(j + NST, pn);
+    if (NST == 2)
+      cp_async_wait1();
+    else
+      cp_async_wait0();
     const uint32_t par = (phase_bits >> (2 * g + st)) & 1u;
     if (tc_wait(&bar[st], par)) {
       phase_bits ^= 1u << (2 * g + st);
@@ -830,13 +841,18 @@ __device__ bool bo_apply_phases(const BoArgs<T, IO>& A, BoCta<T>& S, const C<T>*
             }
           break;
         }
-        default:
-          for (int i = 2 * blockIdx.x + team; i < sg.count; i += 2 * gridDim.x) {
+        default: {
+          // inside a GMRES cycle CTA 0 also runs the Arnoldi update at the
+          // start of each step: the upward items go to the other CTAs
+          const int c0 = (A.cycle && gridDim.x > 1) ? 1 : 0;
+          if ((int)blockIdx.x < c0) break;
+          for (int i = 2 * ((int)blockIdx.x - c0) + team; i < sg.count; i += 2 * ((int)gridDim.x - c0)) {
             if (sg.type == SEG_P2M_UP) bo_p2m<T, IO>(A, sg.level, i, true, team_sm, S.cbt[team], tm, xsrc, xs);
             else if (sg.type == SEG_P2M) bo_p2m<T, IO>(A, sg.level, i, false, team_sm, S.cbt[team], tm, xsrc, xs);
             else if (sg.type == SEG_M2M) bo_m2m<T, IO>(A, sg.level, i, team_sm, tm);
           }
           break;
+        }
       }
       __syncthreads();
       if (abort_s) {
@@ -1195,7 +1211,7 @@ struct bnd_op_state {
   int chunk_count[HFMM_MAX_LEVEL + 2] = {};
   int nphase = 0;
   BoPhase ph[BO_MAX_PH];
-  int grid = 0, threads = 0, ng = 0;
+  int grid = 0, threads = 0, ng = 0, nst = 2;
   size_t smem = 0;
 };
 
@@ -1460,13 +1476,15 @@ int bo_plan(fmm_tree* t, bool fp32, cudaStream_t s) {
   bo_schedule(b, L, nact, b->chunk_first, b->chunk_count);
   // launch shape: one CTA per SM, product groups sized to the shared memory
   const size_t csz = fp32 ? sizeof(float2) : sizeof(double2);
-  const size_t group_bytes = 2 * ((size_t)P * P + (size_t)BO_CHUNK * (P + 2)) * csz;
+  const int nst = bo_stages(cfg.R, cfg.RT, (int)csz);
+  const size_t group_bytes = (size_t)nst * ((size_t)P * P + (size_t)BO_CHUNK * (P + 2)) * csz;
   const size_t budget = 200 * 1024;
   const int GT = cfg.RT * 8;
   int ng = (int)std::min<size_t>(std::min(BO_MAX_NG, 512 / GT), budget / group_bytes);
   ng = std::min(ng, bo_groups(cfg.R, cfg.RT, (int)csz));  // the kernel's launch bound
   if (ng < 1) return HFMM_ERR_UNSUPPORTED;
   b->ng = ng;
+  b->nst = nst;
   b->threads = ng * GT;
   // team items (P2M, M2M): two teams, each 16 P + staged weights
   const size_t team_bytes = 2 * csz * (size_t)(16 * P + 8 * BO_MAX_LEAF_PTS);
@@ -1532,6 +1550,7 @@ int bo_launch(fmm_tree* t, const IO* x, IO* y, double scale, cudaStream_t s, int
   A.L = t->L;
   A.nb = b->nb;
   A.ng = b->ng;
+  A.nst = b->nst;
   A.k = T(t->k);
   A.sig = mkc<T>(T(t->sigma_bnd.x), T(t->sigma_bnd.y));
   A.borig = b->borig;

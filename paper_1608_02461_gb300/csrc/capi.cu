@@ -40,6 +40,8 @@ struct fmm_tree_ext {
   BicgWork bicg;     // A x = b by BiCGSTAB
   PrecGraph pg;
   void* dl_work = nullptr;  // [max(n_vol, n_bnd)] complex128: double-layer sums of the BEM solve with data
+  void* gk_phi = nullptr;   // [n_vol] complex128: dphi/dk of fmm_grad_k
+  double* gk_part = nullptr;  // [RE_DOT_PARTS] block partials of the k-gradient reductions
 };
 
 // the inner workspaces and boundary vectors of a form
@@ -241,7 +243,11 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   if (const char* v = getenv("HFMM_BASIS_TABLE")) t->use_rtab = atoi(v) != 0;
   if (const char* v = getenv("HFMM_OVERLAP_NEAR")) t->overlap_near = atoi(v) != 0;
   if (const char* v = getenv("HFMM_M2L_TC")) t->use_m2l_tcore = atoi(v);
-  if (const char* v = getenv("HFMM_BND_OP")) t->use_bnd_op = atoi(v) != 0;
+  if (const char* v = getenv("HFMM_BND_OP")) t->use_bnd_op = atoi(v);
+  // 1 (default): the one-kernel boundary operator where it was measured
+  // faster than the stage chain (up to p = 6; at p = 8 the products are
+  // bound by the FP32 FMA rate and the chain's kernels were faster)
+  if (t->use_bnd_op == 1 && P > 36) t->use_bnd_op = 0;
   HFMM_TRY(tree_alloc(t, &t->m2l_part, csz * t->total_cells * P * t->m2l_part_max));
   HFMM_TRY(tree_alloc_t(t, &t->g_bnd, t->n_bnd + 1));
   HFMM_TRY(tree_alloc_t(t, &t->q_bnd, t->n_bnd + 1));
@@ -394,6 +400,47 @@ extern "C" int fmm_apply(fmm_tree* t, int src_set, int tgt_set, const void* d_q_
   }
   HFMM_CUDA_TRY(cudaEventRecord(t->ev1, s));
   return HFMM_OK;
+}
+
+// smallest order >= p_min with p >= ceil(k rho_2) + 1, rho_2 = sqrt(3)/8 the
+// half-diagonal of the level-2 cells of the unit cube (the coarsest level
+// with M2L); raised to even
+extern "C" int hfmm_order_for_k(double k, int p_min) {
+  if (!(k >= 0.0) || !(k < 1e6) || p_min < 1 || p_min > HFMM_MAX_P) return HFMM_ERR_INVALID_ARG;
+  const double rho2 = std::sqrt(3.0) / 8.0;
+  int p = (int)std::ceil(k * rho2) + 1;
+  if (p & 1) ++p;
+  p = std::max(p, p_min);
+  if (p > HFMM_MAX_P) return HFMM_ERR_UNSUPPORTED;
+  return p;
+}
+
+static int grad_k_scratch(fmm_tree* t, bool phi) {
+  fmm_tree_ext* e = ext_of(t);
+  if (phi && !e->gk_phi) HFMM_TRY(tree_alloc(t, &e->gk_phi, sizeof(double2) * (size_t)t->n_vol));
+  if (!e->gk_part) HFMM_TRY(tree_alloc(t, (void**)&e->gk_part, sizeof(double) * RE_DOT_PARTS));
+  return HFMM_OK;
+}
+
+// dL/dk = Re sum_i conj(g_i) (dG~/dk q)_i on the volume points: the tangent
+// apply into the handle's scratch, then a fixed-order device reduction
+extern "C" int fmm_grad_k(fmm_tree* t, const void* d_q_vol, const void* d_g_vol, double* d_out, void* stream) {
+  if (!t || !d_q_vol || !d_g_vol || !d_out || t->n_vol == 0) return HFMM_ERR_INVALID_ARG;
+  HFMM_TRY(grad_k_scratch(t, true));
+  fmm_tree_ext* e = ext_of(t);
+  HFMM_TRY(fmm_apply(t, HFMM_SET_VOL, HFMM_SET_VOL, d_q_vol, nullptr, e->gk_phi, nullptr, HFMM_DK, stream));
+  return re_dot_dev((const double2*)d_g_vol, (const double2*)e->gk_phi, t->n_vol, 1.0, e->gk_part, d_out,
+                    (cudaStream_t)stream);
+}
+
+// dL/dk of x = A(k)^-1 b given the adjoint solution lam: A = A^T is real for
+// real k and dA/dk = -2k I (Sec. 2), so dL/dk = -Re <lam, dA/dk x> = 2k Re <lam, x>
+extern "C" int hfmm_solve_grad_k(fmm_tree* t, const void* d_lam, const void* d_x, double* d_out, void* stream) {
+  if (!t || !d_lam || !d_x || !d_out) return HFMM_ERR_INVALID_ARG;
+  if (!t->lattice) return HFMM_ERR_UNSUPPORTED;
+  HFMM_TRY(grad_k_scratch(t, false));
+  return re_dot_dev((const double2*)d_lam, (const double2*)d_x, (int64_t)t->n * t->n * t->n, 2.0 * t->k,
+                    ext_of(t)->gk_part, d_out, (cudaStream_t)stream);
 }
 
 namespace {

@@ -1882,7 +1882,7 @@ template <typename T, int KMODE, bool TILE = false>
 __global__ void __launch_bounds__(LAT_THREADS, sizeof(T) == 4 ? 2 : 1)
     k_p2p_lat(FmmDev<T> d, const int* __restrict__ near_off, int near_count, int src_set, int tgt_set,
               double2 sig_vol, double2 sig_bnd, const int* __restrict__ list, int nlist,
-              const C<T>* __restrict__ tab, uint32_t tab_bytes, const int* __restrict__ lin) {
+              const C<T>* __restrict__ tab, uint32_t tab_bytes, const int* __restrict__ lin, int tpt_max) {
   HFMM_SKIP_IF(d);
   extern __shared__ __align__(128) unsigned char lat_smem[];
   const C<T>* stab = reinterpret_cast<const C<T>*>(lat_smem);
@@ -1966,11 +1966,12 @@ __global__ void __launch_bounds__(LAT_THREADS, sizeof(T) == 4 ? 2 : 1)
     const int nnb = n_nb;
     const int total = nb_pre[nnb];
     // NT consecutive targets per thread share each source read; tpt threads
-    // per group of NT targets take strided shares of the window
+    // per group of NT targets (a power of two up to tpt_max <= 32) take
+    // strided shares of the window
     constexpr int NT = sizeof(T) == 4 ? 4 : 1;
     const int nq = (ntgt + NT - 1) / NT;
     int tpt = 1;
-    while (tpt < 32 && (tpt * 2) * nq <= LAT_THREADS) tpt *= 2;
+    while (tpt < tpt_max && (tpt * 2) * nq <= LAT_THREADS) tpt *= 2;
     const int qslots = LAT_THREADS / tpt;
     const int sub = tid & (tpt - 1);
     for (int qb = 0; qb < nq; qb += qslots) {
@@ -2346,25 +2347,34 @@ int launch_p2p_lat(fmm_tree* t, const FmmDev<T>& d, int src_set, int tgt_set, do
   const int64_t nh = t->lat_half;  // half-table entries, padded to 16 bytes
   const uint32_t tab_bytes = (uint32_t)(nh * sizeof(C<T>));
   const size_t smem = tab_bytes + (size_t)LAT_WS * sizeof(LatSrc<T>);
+  // the autotuner's choice for this pass, else the defaults
+  const int ci = 3 * (tgt_set - 1) + (src_set - 1);
+  const bool tuned = t->tuned_p2p_tpt[ci] > 0;
+  const bool tile = tuned ? t->tuned_p2p_tile[ci] != 0 : t->lat_tile != 0;
+  const int tpt_max = tuned ? t->tuned_p2p_tpt[ci] : 32;
   auto kern = k_p2p_lat<T, KMODE, false>;
   if constexpr (sizeof(T) == 4) {
-    if (t->lat_tile) kern = k_p2p_lat<T, KMODE, true>;
+    if (tile) kern = k_p2p_lat<T, KMODE, true>;
   }
   HFMM_TRY(set_smem<T>((const void*)kern, smem));
   int per_sm = 0;
   HFMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LAT_THREADS, smem));
   if (per_sm < 1) return HFMM_ERR_UNSUPPORTED;
-  // boundary-only near field on the side stream (concurrent with the far
-  // field): one block per SM, so that the far-field kernels find shared
-  // memory next to it (with volume sources the near field is the larger part
-  // and keeps two)
-  if (d.near && !(src_set & HFMM_SET_VOL)) per_sm = 1;
+  if (tuned) {
+    if (t->tuned_p2p_blocks[ci] > 0) per_sm = std::min(per_sm, t->tuned_p2p_blocks[ci]);
+  } else if (d.near && !(src_set & HFMM_SET_VOL)) {
+    // boundary-only near field on the side stream (concurrent with the far
+    // field): one block per SM, so that the far-field kernels find shared
+    // memory next to it (with volume sources the near field is the larger
+    // part and keeps two)
+    per_sm = 1;
+  }
   const int grid = std::min(na, per_sm * sm_count());
   kern<<<grid, LAT_THREADS, smem, s>>>(d, t->near_off, t->near_count, src_set, tgt_set, sv, sb,
                                        act_list(t, tgt_set, t->L), na,
                                        reinterpret_cast<const C<T>*>(sizeof(T) == 4 ? (const void*)t->lat_tab32
                                                                                     : (const void*)t->lat_tab64),
-                                       tab_bytes, t->lat_lin);
+                                       tab_bytes, t->lat_lin, tpt_max);
   return hfmm_last_launch();
 }
 

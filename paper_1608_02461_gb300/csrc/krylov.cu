@@ -17,6 +17,7 @@ namespace {
 constexpr int RT = 128;      // threads of the reduction kernels
 constexpr int RMAXB = 608;   // at most 4 reduction blocks per SM (152 SMs)
 constexpr int KV = 8;        // vectors accumulated per pass over a block's elements
+static_assert(RMAXB <= RE_DOT_PARTS, "re_dot_dev's scratch holds one partial per block");
 
 static inline int red_blocks(int64_t N) {
   int64_t b = (N + RT - 1) / RT;
@@ -427,6 +428,53 @@ void gmres_work_free(GmresWorkT<R>& W) {
   if (W.base) cudaFree(W.base);
   if (W.host) cudaFreeHost(W.host);
   W = GmresWorkT<R>();
+}
+
+namespace {
+
+// out = scale Re sum_i conj(a_i) b_i in FP64: each thread sums its strided
+// elements in index order, each block folds its threads in a fixed tree and
+// writes one partial; k_re_dot_final adds the partials in block order, so
+// the result does not depend on the order in which blocks run
+__global__ void __launch_bounds__(RT) k_re_dot_part(const double2* __restrict__ a, const double2* __restrict__ b,
+                                                    int64_t N, double* __restrict__ part) {
+  __shared__ double sh[RT / 32];
+  const int64_t stride = (int64_t)gridDim.x * RT;
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)RT + threadIdx.x; e < N; e += stride) {
+    const double2 x = a[e], y = b[e];
+    acc = fma(x.x, y.x, acc);
+    acc = fma(x.y, y.y, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < RT / 32; ++w) s += sh[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(32) k_re_dot_final(const double* __restrict__ part, int nb, double scale,
+                                                     double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) acc += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (threadIdx.x == 0) *out = scale * acc;
+}
+
+}  // namespace
+
+int re_dot_dev(const double2* a, const double2* b, int64_t N, double scale, double* part, double* out,
+               cudaStream_t s) {
+  const int nb = red_blocks(N);
+  k_re_dot_part<<<nb, RT, 0, s>>>(a, b, N, part);
+  k_re_dot_final<<<1, 32, 0, s>>>(part, nb, scale, out);
+  count_launches(2);
+  return hfmm_last_launch();
 }
 
 template <typename R>

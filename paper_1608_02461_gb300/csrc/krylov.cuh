@@ -62,6 +62,12 @@ int gmres_run(GmresWorkT<R>& W, const DevOpT<R>& A, const DevOpT<R>* M, const C<
 template <typename R>
 int dev_norm(GmresWorkT<R>& W, const C<R>* x, int64_t N, double* out_dev, cudaStream_t s);
 
+// *out = scale Re sum_i conj(a_i) b_i over N complex128 entries (device
+// pointers), deterministic; part: RE_DOT_PARTS doubles of scratch
+constexpr int RE_DOT_PARTS = 608;
+int re_dot_dev(const double2* a, const double2* b, int64_t N, double scale, double* part, double* out,
+               cudaStream_t s);
+
 // One GMRES cycle of m steps from x0 = 0 for capture in a CUDA graph: no
 // host reads; once the device flag *d_done is set (converged or breakdown)
 // the kernels of the remaining steps return at once (the operator's kernels

@@ -194,6 +194,12 @@ struct fmm_tree {
   // variant -1: not tuned (use the defaults above)
   int tuned_variant[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
   int tuned_fill[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // autotuned lattice near field per (target mask, source mask) pair, same
+  // index: tiled form (FP32), cap on the threads per target group (power of
+  // two, 0: not tuned, use the defaults), blocks per SM (0: as many as fit)
+  int tuned_p2p_tile[9] = {};
+  int tuned_p2p_tpt[9] = {};
+  int tuned_p2p_blocks[9] = {};
 
   // ---- near-field kernel table of lattice trees: every point is a node of
   //      the lattice h Z^3, so the kernel between two points depends only on
@@ -267,7 +273,8 @@ struct fmm_tree {
   void* phis = nullptr;         // [n_pts] sorted potentials
 
   // ---- boundary -> boundary apply of the inner solve as one persistent
-  //      kernel (plan built on first use); use_bnd_op 0: the stage chain
+  //      kernel (plan built on first use); use_bnd_op 0: the stage chain,
+  //      1: the kernel up to P = 36, 2: the kernel for every P it supports
   bnd_op_state* bop = nullptr;
   int use_bnd_op = 1;
   int bnd_op_suspend = 0;       // set while the handle runs inside gmres_solve_batched

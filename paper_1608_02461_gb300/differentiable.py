@@ -6,7 +6,8 @@ boundary correction), G~ the truncated FMM operator of Sec. 5.1.2 for the
 tree's wavenumber k.  The backward pass is hand-written through the C ABI:
 
   dL/dq = G~^H (dL/dphi)                      (fmm_apply, HFMM_ADJ)
-  dL/dk = Re sum conj(dL/dphi) * dG~/dk q     (fmm_apply, HFMM_DK)
+  dL/dk = Re sum conj(dL/dphi) * dG~/dk q     (fmm_grad_k: HFMM_DK apply and
+                                               the sum, on the device)
 
 following PyTorch's convention for complex tensors (the gradient of a real
 loss is the conjugate Wirtinger derivative times two, so a linear map's
@@ -38,8 +39,7 @@ class HelmholtzFMM(torch.autograd.Function):
         if ctx.needs_input_grad[0]:
             grad_q, _ = tree.apply(g, None, src=hfmm.SET_VOL, tgt=hfmm.SET_VOL, mode=hfmm.ADJ)
         if ctx.needs_input_grad[1]:
-            dphi, _ = tree.apply(q.contiguous(), None, src=hfmm.SET_VOL, tgt=hfmm.SET_VOL, mode=hfmm.DK)
-            grad_k = (g.conj() * dphi).real.sum().to(torch.float64)
+            grad_k = tree.grad_k(q.contiguous(), g)
         return grad_q, grad_k, None
 
 
@@ -55,7 +55,7 @@ class HelmholtzSolve(torch.autograd.Function):
     is solved the same way (the preconditioner changes the convergence, not
     the solution):
 
-      dL/db = lam,    dL/dk = Re <lam, 2k x>     (dA/dk = -2k I)
+      dL/db = lam,    dL/dk = Re <lam, 2k x>     (dA/dk = -2k I; hfmm_solve_grad_k)
 
     with <u, v> = sum conj(u) v, in PyTorch's convention for complex tensors."""
 
@@ -66,7 +66,6 @@ class HelmholtzSolve(torch.autograd.Function):
         x, info = tree.gmres(b.contiguous(), raise_on_nonconvergence=True, **kw)
         ctx.tree = tree
         ctx.kw = kw
-        ctx.k = float(k)
         ctx.save_for_backward(x)
         return x
 
@@ -77,7 +76,7 @@ class HelmholtzSolve(torch.autograd.Function):
         grad_b = lam if ctx.needs_input_grad[0] else None
         grad_k = None
         if ctx.needs_input_grad[1]:
-            grad_k = (lam.conj() * (2.0 * ctx.k) * x).real.sum().to(torch.float64)
+            grad_k = ctx.tree.solve_grad_k(lam, x)
         return grad_b, grad_k, None, None
 
 

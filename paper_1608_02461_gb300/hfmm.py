@@ -79,6 +79,11 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "hfmm_fdm_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
+    "hfmm_order_for_k": (ctypes.c_int, [ctypes.c_double, ctypes.c_int]),
+    "fmm_grad_k": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
+    "hfmm_solve_grad_k": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     "bem_solve_dirichlet": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
@@ -276,6 +281,27 @@ class Tree:
                "hfmm_fdm_apply")
         return out
 
+    def grad_k(self, q, g, stream=None):
+        """fmm_grad_k: Re sum conj(g) (dG~/dk q) on the volume points, as a
+        float64 CUDA scalar tensor."""
+        torch = _torch()
+        _dev_c128(q, self.n_vol, "q")
+        _dev_c128(g, self.n_vol, "g")
+        out = torch.empty((), dtype=torch.float64, device=q.device)
+        _check(lib().fmm_grad_k(self._h, _ptr(q), _ptr(g), _ptr(out), _stream_ptr(stream)), "fmm_grad_k")
+        return out
+
+    def solve_grad_k(self, lam, x, stream=None):
+        """hfmm_solve_grad_k: 2k Re sum conj(lam) x, as a float64 CUDA scalar
+        tensor."""
+        torch = _torch()
+        _dev_c128(lam, self.n_vol, "lam")
+        _dev_c128(x, self.n_vol, "x")
+        out = torch.empty((), dtype=torch.float64, device=x.device)
+        _check(lib().hfmm_solve_grad_k(self._h, _ptr(lam), _ptr(x), _ptr(out), _stream_ptr(stream)),
+               "hfmm_solve_grad_k")
+        return out
+
     def gmres(self, b, x=None, restart=30, rtol=1e-6, maxit=0, inner_rtol=1e-4, inner_maxit=200,
               inner_m=50, history_len=2000, raise_on_nonconvergence=False, stream=None):
         torch = _torch()
@@ -371,6 +397,15 @@ def gmres_solve_batched(trees, bs, xs=None, restart=50, rtol=1e-6, maxit=0, inne
     out = [GmresInfo(i.iters, i.restarts, i.inner_iters_total, i.status, i.relres_est, i.relres_true,
                      list(hist[j][:min(i.iters, history_len)])) for j, i in enumerate(infos)]
     return xs, out
+
+
+def order_for_k(k: float, p_min: int) -> int:
+    """hfmm_order_for_k: the expansion order to build a tree with for
+    wavenumber k when at least p_min is asked for."""
+    st = lib().hfmm_order_for_k(float(k), int(p_min))
+    if st < 1:
+        raise HfmmError(st, "hfmm_order_for_k")
+    return st
 
 
 def check_noalloc_args(src_xyz, q, tgt_xyz, phi, require_cuda=True):

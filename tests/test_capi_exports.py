@@ -2,6 +2,7 @@
 declared in include/hfmm.h with the binding's signature table covering them
 all.  No compute calls: this runs without a GPU."""
 import ctypes
+import numpy as np
 import os
 import re
 
@@ -82,6 +83,8 @@ def test_invalid_arguments_rejected_without_gpu(built_lib):
     assert L.hfmm_dirichlet_rhs(None, None, None, None, None) == hfmm.HFMM_ERR_INVALID_ARG
     assert L.bem_solve_dirichlet(None, None, None, None, 1e-2, 20, 20, None, None) == hfmm.HFMM_ERR_INVALID_ARG
     assert L.fmm_set_inner_order(None, 4, None) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.fmm_grad_k(None, None, None, None, None) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.hfmm_solve_grad_k(None, None, None, None, None) == hfmm.HFMM_ERR_INVALID_ARG
 
 
 def test_binding_prototypes_match_header_arity():
@@ -134,3 +137,30 @@ def test_noalloc_binding_rejects_bad_arguments_before_launch():
                 phi=torch.zeros(big, dtype=torch.complex128))
     with pytest.raises(ValueError):
         hfmm.check_noalloc_args(**args, require_cuda=False)
+
+
+def test_order_for_k_rule(built_lib):
+    """hfmm_order_for_k (host only): the smallest even order >= p_min with
+    p >= ceil(k sqrt(3)/8) + 1.  The named workloads keep their orders; the
+    batched solves that stalled at p = 4 (k >= 21.75) get 6 or 8."""
+    import math
+    from paper_1608_02461_gb300 import hfmm
+    for k, p in [(4.0, 4), (16.0, 6), (32.0, 8), (12.0, 6)]:
+        assert hfmm.order_for_k(k, p) == p
+    assert hfmm.order_for_k(21.754, 4) == 6
+    assert hfmm.order_for_k(26.091, 4) == 8
+    assert hfmm.order_for_k(30.95, 4) == 8
+    assert hfmm.order_for_k(30.84, 6) == 8
+    assert hfmm.order_for_k(13.745, 4) == 4
+    assert hfmm.order_for_k(0.0, 3) == 3
+    for k in np.linspace(0.0, 60.0, 241):
+        for pmin in (1, 4, 5, 6):
+            p = hfmm.order_for_k(k, pmin)
+            need = math.ceil(k * math.sqrt(3.0) / 8.0) + 1
+            assert p >= pmin and p >= need
+            assert p == pmin or (p % 2 == 0 and p - 2 < max(need, pmin))
+    L = hfmm.lib()
+    assert L.hfmm_order_for_k(-1.0, 4) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.hfmm_order_for_k(float("nan"), 4) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.hfmm_order_for_k(5.0, 0) == hfmm.HFMM_ERR_INVALID_ARG
+    assert L.hfmm_order_for_k(200.0, 4) == hfmm.HFMM_ERR_UNSUPPORTED

@@ -25,7 +25,7 @@ def rel(a, b):
 
 def tree(n, k, p, theta, leaf, prec, bnd_op=True):
     old = os.environ.get("HFMM_BND_OP")
-    os.environ["HFMM_BND_OP"] = "1" if bnd_op else "0"
+    os.environ["HFMM_BND_OP"] = "2" if bnd_op else "0"
     try:
         return hfmm.Tree(n, k, p, theta, leaf, prec)
     finally:

@@ -172,3 +172,30 @@ def test_gradient_through_the_solve():
     tm = hfmm.Tree(n, k - hk, p, 0.4, 8, "fp64")
     fdk = (loss(tp, b) - loss(tm, b)) / (2 * hk)
     assert abs(fdk - gk) <= 1e-6 * abs(gk), (fdk, gk)
+
+
+def test_grad_k_entry_points():
+    """fmm_grad_k against the GPU tangent apply summed on the host (1e-13)
+    and against the oracle's FMM differenced in k (1e-7); hfmm_solve_grad_k
+    against 2k Re <lam, x> on the host; both bit-identical on a second call."""
+    n, k, p, leaf, h = 8, 4.0, 5, 8, 1e-5
+    tree = hfmm.Tree(n, k, p, 0.4, leaf, "fp64")
+    q, g = cvec(n ** 3, 21), cvec(n ** 3, 22)
+    gk = tree.grad_k(q, g)
+    assert gk.is_cuda and gk.dtype == torch.float64 and gk.dim() == 0
+    gh = g.cpu().numpy()
+    ref = np.real(np.vdot(gh, apply(tree, q, None, 1, 1, mode=hfmm.DK)))
+    assert abs(gk.item() - ref) <= 1e-13 * abs(ref), (gk.item(), ref)
+    assert torch.equal(gk, tree.grad_k(q, g))
+    op = bem.Problem(n, k + h, p, leaf, 0.4)
+    om = bem.Problem(n, k - h, p, leaf, 0.4)
+    qf = np.concatenate([q.cpu().numpy(), np.zeros(op.NG, dtype=np.complex128)])
+    dphi = (op.fmm.apply(qf, op.vol, op.vol, op.sigma) - om.fmm.apply(qf, om.vol, om.vol, om.sigma)) / (2 * h)
+    oref = np.real(np.vdot(gh, dphi[op.vol]))
+    assert abs(gk.item() - oref) <= 1e-7 * abs(oref), (gk.item(), oref)
+    lam, x = cvec(n ** 3, 23), cvec(n ** 3, 24)
+    sk = tree.solve_grad_k(lam, x)
+    sref = 2 * k * np.real(np.vdot(lam.cpu().numpy(), x.cpu().numpy()))
+    assert abs(sk.item() - sref) <= 1e-13 * abs(sref), (sk.item(), sref)
+    assert torch.equal(sk, tree.solve_grad_k(lam, x))
+    tree.close()

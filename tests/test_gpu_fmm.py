@@ -282,7 +282,8 @@ def test_concurrent_near_field_is_bitwise_equal(prec):
 def test_tensor_core_m2l_matches_cuda_core(p):
     """The FP32 form's far field at levels >= 4 on the tensor cores (tcgen05,
     TF32 inputs split hi + lo, three products) against the CUDA-core M2L of
-    the same form and against the FP64 form: both within the FP32 bound."""
+    the same form, against the FP64 form and against the oracle's FMM: all
+    within the FP32 bound."""
     n, k, leaf = 32, 9.0, 8  # L = 4
     tc = hfmm.Tree(n, k, p, 0.4, leaf, "fp32")
     cc = _tree_with_env({"HFMM_M2L_TC": "0"}, n, k, p, 0.4, leaf, "fp32")
@@ -296,6 +297,11 @@ def test_tensor_core_m2l_matches_cuda_core(p):
         c = run_apply(f64, qv if src & 1 else None, qb if src & 2 else None, src, tgt)
         assert rel(a, c) < 3e-5, (src, tgt, rel(a, c))
         assert rel(b, c) < 3e-5
+    pr = bem.Problem(n, k, p, leaf, 0.4)
+    assert pr.fmm.L == 4
+    ref = oracle_apply(pr, qv, qb, 3, 3)
+    got = run_apply(tc, qv, qb, 3, 3)
+    assert rel(got, ref) < 3e-5, rel(got, ref)
     # repeated applies are bitwise identical (fixed summation order)
     a2 = run_apply(tc, qv, qb, 3, 3)
     assert np.array_equal(a2, run_apply(tc, qv, qb, 3, 3))
