@@ -187,7 +187,8 @@ __device__ bool bo_grid_sync(unsigned* bar, unsigned& gen) {
   return ok_s != 0;
 }
 
-// the last CTA to leave resets the barrier words for the next launch
+// the last CTA to leave resets the barrier words and the item counters
+// (bar[4 ...]) for the next launch
 __device__ void bo_exit(unsigned* bar) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -195,6 +196,7 @@ __device__ void bo_exit(unsigned* bar) {
     if (atomicAdd(&bar[3], 1u) == gridDim.x - 1) {
       bar[0] = 0u;
       bar[2] = 0u;
+      for (int i = 0; i < BO_MAX_PH * BO_MAX_SEG; ++i) bar[4 + i] = 0u;
       __threadfence();
       bar[3] = 0u;
     }
@@ -237,9 +239,11 @@ __device__ __forceinline__ C<T> weight(const BoArgs<T, IO>& A, int i) {
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// one arrival on the mbarrier once this thread's earlier cp.async copies have
+// landed (counted in the barrier's expected arrivals)
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(sa(bar)) : "memory");
+}
 // named barriers: 1 .. BO_MAX_NG for the thread groups of the product and
 // downward items, 8 and 9 for the two teams of the upward items
 __device__ __forceinline__ void group_sync(int g, int nthreads) {
@@ -626,123 +630,130 @@ __device__ __forceinline__ void bo_prod_cols(const BoArgs<T, IO>& A, const C<T>*
     }
 }
 
+// records of a product chunk in shared memory: the header {level, slot,
+// first, count}, the pair (product row) and the source row of each column
+struct __align__(16) BoRec {
+  int4 ch;
+  int pid[BO_CHUNK];
+  int row[BO_CHUNK];
+};
+constexpr int BO_NBAR = 5;  // mbarriers per group: two stages, three record slots
+
 // group items SEG_PROD: chunk i of [first, first + count) -> buf rows, per
-// group of GT = RT * 8 threads; two stages (operator by bulk copy on an
-// mbarrier, source rows by cp.async), the items two ahead fetched while the
-// current one is multiplied; chunk headers and the pairs' row indices go to
-// shared memory with the fetch.  Returns false on a wait time-out.
+// group of GT = RT * 8 threads.  Every copy completes on an mbarrier: the
+// records of the item three ahead (bulk copies) into one of three record
+// slots, and for the item NST ahead the operator (one bulk copy) and the
+// source rows (16-byte cp.async by every thread of the group, from the
+// records, each thread arriving once when its copies have landed: stage
+// barriers expect 1 + GT arrivals) into one of NST stages, so that all
+// latencies overlap the products of the current item.  Every thread of the
+// group waits for each completion it reads (and all track the barriers'
+// phases alike).  Returns false on a wait time-out.
 template <typename T, typename IO, int R, int CM, int RT>
 __device__ bool bo_products(const BoArgs<T, IO>& A, const BoSeg& sg, unsigned char* sm, uint64_t* mbar,
-                            uint32_t& phase_bits, int* gabort, int4 (*chs)[2], int (*gpid)[2][BO_CHUNK]) {
+                            uint32_t& phase_bits, int* gabort, BoRec (*rec)[3]) {
   constexpr int GT = RT * 8, CT = 8, TC = CT * CM;
   static_assert(TC == BO_CHUNK, "one product column per pair of a chunk");
-  constexpr int ROW16 = (R * RT * (int)sizeof(C<T>)) / 16;  // 16-byte pieces of the longest row
-  constexpr int KMAX = (TC * ROW16 + GT - 1) / GT;
+  static_assert(BO_NBAR * BO_MAX_NG <= 32, "phase bits of every group in one word");
   const int P = A.P, MS = P + 2;
   const int g = threadIdx.x / GT, tg = threadIdx.x - g * GT;
   if (g >= A.ng) return true;
   const size_t op_elems = (size_t)P * P, ms_elems = (size_t)TC * MS;
   const int NST = A.nst;
   C<T>* base = reinterpret_cast<C<T>*>(sm) + (size_t)g * NST * (op_elems + ms_elems);
-  C<T>* Ts0 = base;
-  C<T>* Ms0 = base + op_elems;
-  C<T>* Ts1 = base + op_elems + ms_elems;  // second stage (NST == 2)
-  C<T>* Ms1 = Ts1 + op_elems;
-  uint64_t* bar = mbar + 2 * g;
+  uint64_t* bar = mbar + BO_NBAR * g;  // [0, 2): stages, [2, 5): record slots
   const int gid = blockIdx.x * A.ng + g, ngt = gridDim.x * A.ng;
+  const int nitems = gid < sg.count ? (sg.count - gid + ngt - 1) / ngt : 0;
   const uint32_t op_bytes = (uint32_t)(op_elems * sizeof(C<T>));
-  const int row16 = (int)(P * sizeof(C<T>) / 16);
-  const int end = sg.first + sg.count;
-  uint32_t pending = 0;  // stages with an operator copy in flight
-  // the fetch of an item in two steps: its records into registers (issued
-  // one item ahead, so that their latency overlaps the current product),
-  // then the copies from those registers
-  struct Pre {
-    int4 ch;
-    int pid;
-    int row[KMAX];
+  const uint32_t row_bytes = (uint32_t)(P * sizeof(C<T>));
+  auto bit = [&](int k) { return 1u << (BO_NBAR * g + k); };
+  auto par = [&](int k) { return (phase_bits & bit(k)) ? 1u : 0u; };
+  uint32_t pending = 0;  // barriers with a phase issued and not yet consumed
+  auto fail = [&]() {
+    atomicExch(&g_bo_error, HFMM_ERR_TIMEOUT);
+    *(volatile int*)&gabort[g] = 1;
   };
-  auto preload = [&](int j, Pre& pr) {
-    const int it = sg.first + gid + j * ngt;
-    pr.ch = make_int4(-1, 0, 0, 0);
-    if (it < end) {
-      pr.ch = A.chunks[it];
-      pr.pid = tg < TC ? A.cpid[(int64_t)it * TC + tg] : -1;
-#pragma unroll
-      for (int kk = 0; kk < KMAX; ++kk) {
-        const int c = (tg + kk * GT) / row16;
-        pr.row[kk] = c < TC ? A.crow[(int64_t)it * TC + c] : -1;
-      }
+  // records of item j into slot j % 3
+  auto rec_issue = [&](int j) {
+    if (j >= nitems) return;
+    const int s = j % 3, it = sg.first + gid + j * ngt;
+    if (tg == 0) {
+      uint64_t* rb = &bar[2 + s];
+      tc_expect_tx(rb, (uint32_t)sizeof(BoRec));
+      tc_bulk_g2s(&rec[g][s].ch, A.chunks + it, 16, rb);
+      tc_bulk_g2s(rec[g][s].pid, A.cpid + (int64_t)it * TC, 4 * TC, rb);
+      tc_bulk_g2s(rec[g][s].row, A.crow + (int64_t)it * TC, 4 * TC, rb);
     }
+    pending |= bit(2 + s);
   };
-  auto issue = [&](int st, const Pre& pr) {
-    if (pr.ch.x >= 0) {
-      C<T>* Ts = st ? Ts1 : Ts0;
-      C<T>* Ms = st ? Ms1 : Ms0;
+  // operator and source rows of item j into stage j % NST (every thread
+  // waits for the records of item j without consuming that phase)
+  const int row16 = (int)(row_bytes / 16);
+  auto stage_issue = [&](int j) {
+    if (j >= nitems) return;
+    const int st = j % NST, s = j % 3;
+    if (tc_wait(&bar[2 + s], par(2 + s))) {
+      C<T>* Ts = base + (size_t)st * (op_elems + ms_elems);
+      C<T>* Ms = Ts + op_elems;
+      const int4 ch = rec[g][s].ch;
       if (tg == 0) {
-        chs[g][st] = pr.ch;
         tc_expect_tx(&bar[st], op_bytes);
-        tc_bulk_g2s(Ts, A.m2l + ((int64_t)pr.ch.x * A.box_cells + pr.ch.y) * P * P, op_bytes, &bar[st]);
+        tc_bulk_g2s(Ts, A.m2l + ((int64_t)ch.x * A.box_cells + ch.y) * P * P, op_bytes, &bar[st]);
       }
-      if (tg < TC) gpid[g][st][tg] = pr.pid;
-      pending |= 1u << st;
-#pragma unroll
-      for (int kk = 0; kk < KMAX; ++kk) {
-        const int e = tg + kk * GT;
-        if (pr.row[kk] >= 0 && e < TC * row16) {
-          const int c = e / row16, pc = e - c * row16;
-          cp_async16(reinterpret_cast<unsigned char*>(Ms + (size_t)c * MS) + 16 * pc,
-                     reinterpret_cast<const unsigned char*>(A.M + (int64_t)pr.row[kk] * P) + 16 * pc);
-        }
+      for (int e = tg; e < ch.w * row16; e += GT) {
+        const int c = e / row16, pc = e - c * row16;
+        cp_async16(reinterpret_cast<unsigned char*>(Ms + (size_t)c * MS) + 16 * pc,
+                   reinterpret_cast<const unsigned char*>(A.M + (int64_t)rec[g][s].row[c] * P) + 16 * pc);
       }
-    }
-    cp_async_commit();
-  };
-  {
-    Pre p0, p1;
-    preload(0, p0);
-    if (NST == 2) preload(1, p1);
-    issue(0, p0);
-    if (NST == 2) issue(1, p1);
-  }
-  bool ok = true;
-  for (int j = 0; sg.first + gid + j * ngt < end; ++j) {
-    const int st = NST == 2 ? (j & 1) : 0;
-    Pre pn;
-    preload(j + NST, pn);
-    if (NST == 2)
-      cp_async_wait1();
-    else
-      cp_async_wait0();
-    const uint32_t par = (phase_bits >> (2 * g + st)) & 1u;
-    if (tc_wait(&bar[st], par)) {
-      phase_bits ^= 1u << (2 * g + st);
-      pending &= ~(1u << st);
+      cp_async_arrive_noinc(&bar[st]);
     } else {
-      atomicExch(&g_bo_error, HFMM_ERR_TIMEOUT);
-      gabort[g] = 1;
+      fail();
     }
+    pending |= bit(st);
+  };
+  for (int j = 0; j < 3; ++j) rec_issue(j);
+  for (int j = 0; j < NST; ++j) stage_issue(j);
+  bool ok = true;
+  for (int j = 0; j < nitems; ++j) {
+    const int st = j % NST, s = j % 3;
+    // every thread reads the records (width, pair rows) and the stage
+    bool w = tc_wait(&bar[2 + s], par(2 + s));
+    if (w) {
+      phase_bits ^= bit(2 + s);
+      pending &= ~bit(2 + s);
+      w = tc_wait(&bar[st], par(st));
+      if (w) {
+        phase_bits ^= bit(st);
+        pending &= ~bit(st);
+      }
+    }
+    if (!w) fail();
     group_sync(g, GT);
     if (*(volatile int*)&gabort[g]) {
       ok = false;
       break;
     }
-    const int cw = chs[g][st].w;
+    C<T>* Ts = base + (size_t)st * (op_elems + ms_elems);
+    C<T>* Ms = Ts + op_elems;
+    const int cw = rec[g][s].ch.w;
+    const int* pids = rec[g][s].pid;
     const int r0 = tg / CT, c0 = tg % CT;
     // only the column groups the chunk fills
     switch ((cw + CT - 1) / CT) {
-      case 1: bo_prod_cols<T, IO, R, 1, RT>(A, st ? Ts1 : Ts0, st ? Ms1 : Ms0, gpid[g][st], cw, r0, c0); break;
-      case 2: bo_prod_cols<T, IO, R, 2, RT>(A, st ? Ts1 : Ts0, st ? Ms1 : Ms0, gpid[g][st], cw, r0, c0); break;
-      case 3: bo_prod_cols<T, IO, R, 3, RT>(A, st ? Ts1 : Ts0, st ? Ms1 : Ms0, gpid[g][st], cw, r0, c0); break;
-      default: bo_prod_cols<T, IO, R, CM, RT>(A, st ? Ts1 : Ts0, st ? Ms1 : Ms0, gpid[g][st], cw, r0, c0); break;
+      case 1: bo_prod_cols<T, IO, R, 1, RT>(A, Ts, Ms, pids, cw, r0, c0); break;
+      case 2: bo_prod_cols<T, IO, R, 2, RT>(A, Ts, Ms, pids, cw, r0, c0); break;
+      case 3: bo_prod_cols<T, IO, R, 3, RT>(A, Ts, Ms, pids, cw, r0, c0); break;
+      default: bo_prod_cols<T, IO, R, CM, RT>(A, Ts, Ms, pids, cw, r0, c0); break;
     }
-    group_sync(g, GT);
-    issue(st, pn);
+    group_sync(g, GT);  // stage st and record slot s are free again
+    rec_issue(j + 3);
+    stage_issue(j + NST);
   }
-  cp_async_wait0();
-  // operator copies still in flight (after a time-out): let them land, bounded
-  for (int st = 0; st < 2; ++st)
-    if ((pending >> st) & 1u) tc_wait(&bar[st], (phase_bits >> (2 * g + st)) & 1u);
+  if (!ok) {
+    // copies still in flight after a time-out: let them land, bounded
+    for (int k = 0; k < BO_NBAR; ++k)
+      if (pending & bit(k)) tc_wait(&bar[k], par(k));
+  }
   group_sync(g, GT);
   return ok;
 }
@@ -754,11 +765,12 @@ struct BoCta {
   unsigned char* smem;
   uint64_t* mbar;
   int* gabort;
-  int4 (*chs)[2];
-  int (*gpid)[2][BO_CHUNK];
+  BoRec (*rec)[3];
+  int* gnext;        // [BO_MAX_NG] next item of each group (dynamic segments)
   int (*cbt)[9];
   unsigned gen;
   uint32_t phase_bits;
+  unsigned napply;  // boundary applies finished in this launch
 };
 
 // the phases of one boundary -> boundary apply; xsrc / xs: the input inside a
@@ -798,7 +810,7 @@ __device__ bool bo_apply_phases(const BoArgs<T, IO>& A, BoCta<T>& S, const C<T>*
       const BoSeg sg = Ph.seg[si];
       switch (sg.type) {
         case SEG_PROD:
-          if (!bo_products<T, IO, R, CM, RT>(A, sg, S.smem, S.mbar, S.phase_bits, S.gabort, S.chs, S.gpid))
+          if (!bo_products<T, IO, R, CM, RT>(A, sg, S.smem, S.mbar, S.phase_bits, S.gabort, S.rec))
             abort_s = 1;
           break;
         case SEG_DOWN:
@@ -827,8 +839,19 @@ __device__ bool bo_apply_phases(const BoArgs<T, IO>& A, BoCta<T>& S, const C<T>*
             __syncthreads();
           }
           BoNs<T>* ns_st = A.near_win ? reinterpret_cast<BoNs<T>*>(gsm + down_sums) : nullptr;
-          if (g < A.ng)
-            for (int i = blockIdx.x * A.ng + g; i < sg.count; i += gridDim.x * A.ng) {
+          // items handed out one at a time from a counter that grows by
+          // count + (groups of the grid) per apply (every group takes one
+          // index past the end): the item costs differ, and each item owns
+          // its outputs, so results do not depend on which group runs it
+          if (g < A.ng) {
+            unsigned* ctr = A.bar + 4 + ph * BO_MAX_SEG + si;
+            const unsigned base = S.napply * (unsigned)(sg.count + (int)gridDim.x * A.ng);
+            if (tg == 0) S.gnext[g] = (int)(atomicAdd(ctr, 1u) - base);
+            group_sync(g, GT);
+            int i = S.gnext[g];
+            while (i < sg.count) {
+              unsigned nx = 0u;
+              if (tg == 0) nx = atomicAdd(ctr, 1u);  // the next index, while this item runs
               if (sg.type == SEG_DOWN) {
                 bo_down<T, IO>(A, sg.level, i, sg.first, gsm, g, tg, GT, l2l_sm, tab, ns_st);
               } else if (sg.type == SEG_ROWS) {
@@ -836,9 +859,13 @@ __device__ bool bo_apply_phases(const BoArgs<T, IO>& A, BoCta<T>& S, const C<T>*
               } else {
                 const int leafc = A.act[A.loff[A.L] + i];
                 bo_near<T, IO>(A, i, leafc, A.nearv + A.bfirst[leafc], tab, ns_st, g, tg, GT);
-                group_sync(g, GT);
               }
+              group_sync(g, GT);
+              if (tg == 0) S.gnext[g] = (int)(nx - base);
+              group_sync(g, GT);
+              i = S.gnext[g];
             }
+          }
           break;
         }
         default: {
@@ -861,6 +888,7 @@ __device__ bool bo_apply_phases(const BoArgs<T, IO>& A, BoCta<T>& S, const C<T>*
       }
     }
   }
+  S.napply += 1;
   return true;
 }
 
@@ -1164,18 +1192,20 @@ __global__ void __launch_bounds__(RT * 8 * bo_groups(R, RT, (int)sizeof(C<T>)), 
     k_bnd_op(const __grid_constant__ BoArgs<T, IO> A) {
   if (A.skip && *A.skip) return;
   extern __shared__ __align__(128) unsigned char bo_smem[];
-  __shared__ __align__(8) uint64_t mbar[2 * BO_MAX_NG];
+  __shared__ __align__(8) uint64_t mbar[BO_NBAR * BO_MAX_NG];
   __shared__ int gabort[BO_MAX_NG];
-  __shared__ int4 chs[BO_MAX_NG][2];
-  __shared__ int gpid[BO_MAX_NG][2][BO_CHUNK];
+  __shared__ BoRec rec[BO_MAX_NG][3];
+  __shared__ int gnext[BO_MAX_NG];
   __shared__ int cbt[2][9];
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2 * BO_MAX_NG; ++i) tc_mbar_init(&mbar[i], 1);
+    // per group: two stage barriers (the operator's expect-tx arrival and
+    // one cp.async arrival per thread of the group), three record slots
+    for (int i = 0; i < BO_NBAR * BO_MAX_NG; ++i) tc_mbar_init(&mbar[i], (i % BO_NBAR) < 2 ? 1 + RT * 8 : 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int i = 0; i < BO_MAX_NG; ++i) gabort[i] = 0;
   }
   __syncthreads();
-  BoCta<T> S{bo_smem, mbar, gabort, chs, gpid, cbt, 0u, 0u};
+  BoCta<T> S{bo_smem, mbar, gabort, rec, gnext, cbt, 0u, 0u, 0u};
   if (A.cycle)
     bo_cycle<T, IO, R, CM, RT>(A, S);
   else
@@ -1469,16 +1499,32 @@ int bo_plan(fmm_tree* t, bool fp32, cudaStream_t s) {
                                                          (double2*)b->Rb);
   HFMM_TRY(hfmm_last_launch());
   HFMM_CUDA_TRY(cudaStreamSynchronize(s));
-  HFMM_TRY(tree_alloc_t(t, &b->bar, 4));
-  HFMM_CUDA_TRY(cudaMemset(b->bar, 0, 4 * sizeof(unsigned)));
+  // barrier words [0, 4) and the dynamic segments' item counters
+  HFMM_TRY(tree_alloc_t(t, &b->bar, 4 + BO_MAX_PH * BO_MAX_SEG));
+  HFMM_CUDA_TRY(cudaMemset(b->bar, 0, (4 + BO_MAX_PH * BO_MAX_SEG) * sizeof(unsigned)));
   b->nb = (int)t->n_bnd;
   b->nbl = nact[L];
   bo_schedule(b, L, nact, b->chunk_first, b->chunk_count);
   // launch shape: one CTA per SM, product groups sized to the shared memory
   const size_t csz = fp32 ? sizeof(float2) : sizeof(double2);
+  // dynamic shared memory left beside the kernel's static arrays (at most 220 KB)
+  const void* kern = fp32 ? bo_kernel_for<float, float2>(P) : bo_kernel_for<double, double2>(P);
+  const void* kern2 = fp32 ? bo_kernel_for<float, double2>(P) : kern;
+  size_t smem_cap = 220 * 1024;
+  {
+    int dev = 0, optin = 0;
+    HFMM_CUDA_TRY(cudaGetDevice(&dev));
+    HFMM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa1, fa2;
+    HFMM_CUDA_TRY(cudaFuncGetAttributes(&fa1, kern));
+    HFMM_CUDA_TRY(cudaFuncGetAttributes(&fa2, kern2));
+    const size_t stat = std::max(fa1.sharedSizeBytes, fa2.sharedSizeBytes);
+    if ((size_t)optin <= stat) return HFMM_ERR_UNSUPPORTED;
+    smem_cap = std::min(smem_cap, (size_t)optin - stat);
+  }
   const int nst = bo_stages(cfg.R, cfg.RT, (int)csz);
   const size_t group_bytes = (size_t)nst * ((size_t)P * P + (size_t)BO_CHUNK * (P + 2)) * csz;
-  const size_t budget = 200 * 1024;
+  const size_t budget = std::min<size_t>(200 * 1024, smem_cap);
   const int GT = cfg.RT * 8;
   int ng = (int)std::min<size_t>(std::min(BO_MAX_NG, 512 / GT), budget / group_bytes);
   ng = std::min(ng, bo_groups(cfg.R, cfg.RT, (int)csz));  // the kernel's launch bound
@@ -1496,7 +1542,6 @@ int bo_plan(fmm_tree* t, bool fp32, cudaStream_t s) {
   // near-source records, then near_win records)
   const size_t sums = ((size_t)(2 * (GT / (P / 2)) + 2) * P + BO_MAX_LEAF_PTS + 1) / 2 * 2;
   auto down_b = [&](int nw) { return csz * (size_t)ng * (sums + 2 * (size_t)nw); };
-  const size_t smem_cap = 220 * 1024;
   const size_t tab_bytes = csz * (size_t)((t->lat_half + 1) & ~(int64_t)1);
   const size_t l2l_bytes = csz * 8 * (size_t)P * P;
   const bool worth = nact[L] >= 4 * nsm;
@@ -1507,9 +1552,7 @@ int bo_plan(fmm_tree* t, bool fp32, cudaStream_t s) {
   b->stage_l2l = worth && L > 2 && down_b(nw) + (b->stage_tab ? tab_bytes : 0) + l2l_bytes <= smem_cap;
   const size_t down_total = down_b(nw) + (b->stage_tab ? tab_bytes : 0) + (b->stage_l2l ? l2l_bytes : 0);
   b->smem = std::max(std::max((size_t)ng * group_bytes, team_bytes), down_total);
-  const void* kern = fp32 ? bo_kernel_for<float, float2>(P) : bo_kernel_for<double, double2>(P);
   HFMM_TRY(set_smem_any(kern, b->smem));
-  const void* kern2 = fp32 ? bo_kernel_for<float, double2>(P) : kern;
   HFMM_TRY(set_smem_any(kern2, b->smem));
   int per_sm = 0;
   HFMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->threads, b->smem));
