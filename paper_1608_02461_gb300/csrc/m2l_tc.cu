@@ -6,27 +6,30 @@
 // hold zeros).  Every cell of a class shares one M2L offset list (Sec. 5.1.2
 // interaction lists), and for an offset o the sources of a brick of 8 x 4 x 4
 // same-class target cells form a brick of one class at a shifted origin.  So
-// one CTA owns such a brick (128 target cells) and, for each offset of its
-// list, accumulates the real form of the complex product
+// one CTA owns two such bricks stacked in z (8 x 4 x 8 cells, 2 x 128 rows)
+// and, for each offset of its list and each brick, accumulates the real form
+// of the complex product
 //     D[cell][2a'+c'] += sum_k X_src[cell][k] B_o[k][2a'+c'],
 //     B_o[2a][2a'] = B_o[2a+1][2a'+1] = Re T_o(a', a),
 //     B_o[2a][2a'+1] = Im T_o(a', a) = -B_o[2a+1][2a'],
 // with tcgen05.mma (kind::tf32, M = 128 cells, N = 2P rounded up to 16,
-// K = 8 per instruction) into a TMEM accumulator.  The source brick arrives
-// by one 5-D TMA load per 32-float slice of K (zero fill outside the level);
-// the operator slice by a 1-D bulk copy of a pre-swizzled image.  Both use
-// the 128-byte swizzled K-major layout (8-row atoms of 1024 bytes).
+// K = 8 per instruction) into a TMEM accumulator per brick.  The two source
+// bricks arrive by one 5-D TMA load of an 8 x 4 x 8 box per 32-float slice of
+// K (zero fill outside the level; rows x fastest, then y, then z, so the
+// bricks are the box's first and second 128 rows); the operator slice by a
+// 1-D bulk copy of a pre-swizzled image, read by the MMAs of both bricks.
+// All use the 128-byte swizzled K-major layout (8-row atoms of 1024 bytes).
 //
 // FP32 accuracy from TF32 inputs: every operand is split as v = hi + lo with
 // hi = v truncated to TF32 (exact in TF32) and lo = v - hi, and the product is
 // hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).
 //
-// Warp roles (192 threads): warp 4 lane 0 issues the copies of a ring of
-// NSTG stages; warp 5 lane 0 issues the MMAs, commits each stage back to the
+// Warp roles (320 threads): warp 8 lane 0 issues the copies of a ring of
+// NSTG stages; warp 9 lane 0 issues the MMAs, commits each stage back to the
 // producer, and accumulates chunks of CHUNK offsets alternately into two
-// TMEM buffers; warps 0-3 (TMEM lanes 32w..32w+31 = brick cells) add each
-// finished chunk to FP32 registers and free its buffer, then write the
-// result.  Tensor-core accumulation rounds less carefully than FP32 FMA, so
+// TMEM buffers per brick; warps 0-7 (brick w / 4, TMEM lanes 32 (w % 4) ..
+// + 31 = its cells) add each finished chunk to FP32 registers and free its
+// buffer, then write the result.  Tensor-core accumulation rounds less carefully than FP32 FMA, so
 // bounding its chains to one chunk keeps the FP32 form's accuracy.  Every
 // wait is bounded (about one second); on time-out the kernel records
 // HFMM_ERR_TIMEOUT, waits (bounded) for its own copies and MMAs in flight,
@@ -41,13 +44,14 @@
 
 namespace {
 
-constexpr int TC_ACC_WARPS = 4;                      // warps that read TMEM lanes 0..127
+constexpr int TC_ACC_WARPS = 8;                      // warps that read TMEM (two bricks x lanes 0..127)
 constexpr int TC_THREADS = 32 * (TC_ACC_WARPS + 2);  // + producer warp + MMA warp
-constexpr int TC_NSTG = 3;
+constexpr int TC_NSTG = 2;
 constexpr int TC_CHUNK = 8;       // offsets per tensor-core accumulation chain
 constexpr int TC_MAX_NPAD = 128;  // accumulator columns (2P rounded up to 16)
-constexpr int TC_TMEM_COLS = 256; // two accumulator buffers of 128 columns
+constexpr int TC_TMEM_COLS = 512; // per brick two accumulator buffers of 128 columns
 constexpr int BX = 8, BY = 4, BZ = 4;  // brick of same-class target cells (128 rows)
+constexpr int NBRK = 2;                // bricks per CTA, stacked in z
 constexpr int TC_MAX_COUNT = 2048;     // offsets per class list held in shared memory
 
 __device__ int g_tc_error;  // set when a bounded wait gives up
@@ -156,7 +160,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int twoP = 2 * A.P;
-  const uint32_t xbytes = (uint32_t)(BX * BY * BZ * 128);  // one K slice of a brick
+  const uint32_t bxbytes = (uint32_t)(BX * BY * BZ * 128);  // one K slice of a brick
+  const uint32_t xbytes = NBRK * bxbytes;                    // ... of the CTA's bricks
   const uint32_t bbytes = (uint32_t)A.Npad * 128;          // one K slice of an operator
   const uint32_t stage_bytes = 2 * xbytes + 2 * bbytes;
 
@@ -164,11 +169,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
   int level = A.lmin;
   while (level < A.L && (int)blockIdx.x >= A.brick_first[level + 1]) ++level;
   const int h = 1 << (level - 1);
-  const int nbx = h / BX, nby = h / BY, nbz = h / BZ;
+  const int nbx = h / BX, nby = h / BY, nbz = h / (NBRK * BZ);
   int b = (int)blockIdx.x - A.brick_first[level];
   const int cls = b / (nbx * nby * nbz);
   b -= cls * nbx * nby * nbz;
-  const int hz0 = (b / (nbx * nby)) * BZ;
+  const int hz0 = (b / (nbx * nby)) * (NBRK * BZ);
   b %= nbx * nby;
   const int hy0 = (b / nbx) * BY, hx0 = (b % nbx) * BX;
   const int cx = cls & 1, cy = (cls >> 1) & 1, cz = (cls >> 2) & 1;
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
     const int o = A.m2l_off[cls * A.count + i];
     const int ox = (o & 255) - 128, oy = ((o >> 8) & 255) - 128, oz = ((o >> 16) & 255) - 128;
     const int sx = hx0 + ((cx + ox) >> 1), sy = hy0 + ((cy + oy) >> 1), sz = hz0 + ((cz + oz) >> 1);
-    vflag[i - i0] = (sx + BX > 0 && sx < h && sy + BY > 0 && sy < h && sz + BZ > 0 && sz < h) ? 1 : 0;
+    vflag[i - i0] = (sx + BX > 0 && sx < h && sy + BY > 0 && sy < h && sz + NBRK * BZ > 0 && sz < h) ? 1 : 0;
   }
   __syncthreads();
   if (warp == 0) {
@@ -251,9 +256,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
     }
   } else if (warp == TC_ACC_WARPS + 1 && lane == 0) {
     // MMA issuer: chunks of TC_CHUNK offsets into alternating TMEM buffers
+    // (brick q: columns 256 q + 128 buf)
     for (int u = 0; u < units; ++u) {
       const int g = u / cunits, buf = g & 1;
-      const uint32_t dt = tmem + (uint32_t)(buf * 128);
       const bool first = (u % cunits) == 0;
       if (first && g >= 2 && !tc_wait(&drained[buf], (uint32_t)(((g >> 1) - 1) & 1))) {
         atomicExch(&g_tc_error, 1);
@@ -271,14 +276,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
       const int a = u % NA;
       const int kvalid = min(32, twoP - 32 * a);  // K of this slice
       const uint32_t st = sa(smem + (size_t)s * stage_bytes);
-      const uint32_t xh = st, xl = st + xbytes, bh = st + 2 * xbytes, bl = st + 2 * xbytes + bbytes;
-      uint32_t acc = first ? 0u : 1u;
-      for (int kk = 0; kk < kvalid; kk += 8) {
-        const uint32_t ko = (uint32_t)kk * 4;
-        tc_mma(dt, tc_desc(xh + ko), tc_desc(bh + ko), idesc, acc);
-        acc = 1;
-        tc_mma(dt, tc_desc(xh + ko), tc_desc(bl + ko), idesc, 1);
-        tc_mma(dt, tc_desc(xl + ko), tc_desc(bh + ko), idesc, 1);
+      const uint32_t bh = st + 2 * xbytes, bl = st + 2 * xbytes + bbytes;
+      for (int q = 0; q < NBRK; ++q) {
+        const uint32_t dt = tmem + (uint32_t)(q * 256 + buf * 128);
+        const uint32_t xh = st + (uint32_t)q * bxbytes, xl = st + xbytes + (uint32_t)q * bxbytes;
+        uint32_t acc = first ? 0u : 1u;
+        for (int kk = 0; kk < kvalid; kk += 8) {
+          const uint32_t ko = (uint32_t)kk * 4;
+          tc_mma(dt, tc_desc(xh + ko), tc_desc(bh + ko), idesc, acc);
+          acc = 1;
+          tc_mma(dt, tc_desc(xh + ko), tc_desc(bl + ko), idesc, 1);
+          tc_mma(dt, tc_desc(xl + ko), tc_desc(bh + ko), idesc, 1);
+        }
       }
       tc_commit(&empty[s]);  // the stage is free once these MMAs have read it
       if ((u + 1) % cunits == 0 || u + 1 == units) tc_commit(&ready[buf]);  // chunk complete
@@ -300,7 +309,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
         break;
       }
       tc_fence_after();
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 128);
+      const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 256 + buf * 128);
 #pragma unroll
       for (int c0 = 0; c0 < TC_MAX_NPAD; c0 += 16) {
         if (c0 < A.Npad) {
@@ -315,8 +324,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
       if (lane == 0) tc_arrive(&drained[buf]);
     }
     if (good) {
-      const int r = warp * 32 + lane;
-      const int dx = r % BX, dy = (r / BX) % BY, dz = r / (BX * BY);
+      const int r = (warp & 3) * 32 + lane;
+      const int dx = r % BX, dy = (r / BX) % BY, dz = (warp >> 2) * BZ + r / (BX * BY);
       const int X = 2 * (hx0 + dx) + cx, Y = 2 * (hy0 + dy) + cy, Z = 2 * (hz0 + dz) + cz;
       const int64_t cell = A.level_off[level] + (int64_t)morton_encode(X, Y, Z);
       if (A.flags[cell] & A.tgt_set) {
@@ -443,7 +452,7 @@ static int tc_prepare(fmm_tree* t, cudaStream_t s) {
     const cuuint64_t dims[5] = {(cuuint64_t)twoP, hh, hh, hh, 8};
     const cuuint64_t row = (cuuint64_t)twoP * sizeof(float);
     const cuuint64_t strides[4] = {row, row * hh, row * hh * hh, row * hh * hh * hh};
-    const cuuint32_t box[5] = {32, BX, BY, BZ, 1};
+    const cuuint32_t box[5] = {32, BX, BY, NBRK * BZ, 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     for (int w = 0; w < 2; ++w) {
       float* base = (w ? S.xl : S.xh) + S.lat_off[l];
@@ -492,14 +501,14 @@ int m2l_tc_stage(fmm_tree* t, int src_set, int tgt_set, int accumulate, cudaStre
   for (int l = lmin; l <= L; ++l) {
     A.brick_first[l] = nb;
     const int h = 1 << (l - 1);
-    nb += 8 * (h / BX) * (h / BY) * (h / BZ);
+    nb += 8 * (h / BX) * (h / BY) * (h / (NBRK * BZ));
   }
   A.brick_first[L + 1] = nb;
   // split the offset lists until the grid covers the GPU about twice
   const int nsplit = std::max(1, std::min(t->m2l_part_max, (2 * 152 + nb - 1) / nb));
   A.part = nsplit > 1 ? reinterpret_cast<float*>(t->m2l_part) : nullptr;
   A.part_stride = t->total_cells * (int64_t)twoP;
-  const size_t stage_bytes = 2 * (size_t)(BX * BY * BZ * 128) + 2 * (size_t)S.Npad * 128;
+  const size_t stage_bytes = 2 * (size_t)(NBRK * BX * BY * BZ * 128) + 2 * (size_t)S.Npad * 128;
   const size_t smem = TC_NSTG * stage_bytes + 1024;
   HFMM_TRY(set_smem_any((const void*)k_m2l_tc, smem));
   k_m2l_tc<<<dim3(nb, nsplit), TC_THREADS, smem, s>>>(S.maps, A);
