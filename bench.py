@@ -60,7 +60,12 @@ P2P_SMEM_BYTES_PER_PAIR = 12
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_p2p_lat launch (ncu,
 # 64^3 k=16 p=6 FP32 workload) for the three passes of the preconditioner:
 # volume -> boundary, boundary -> boundary, all -> volume
-P2P_DRAM_BYTES = {"A": 2616832, "B": 520704, "C": 5701888}
+P2P_DRAM_BYTES = {"A": 2617088, "B": 520704, "C": 5694976}
+# The boundary operator's kernel (k_bnd_op, one launch = one inner GMRES
+# cycle): dram__bytes_read.sum + dram__bytes_write.sum of one such launch in
+# the benchmark solve (ncu, 64^3 k=16 p=6 FP32, 20 steps), and its steps
+BND_DRAM_BYTES = None
+BND_DRAM_STEPS = 20
 L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 
 
@@ -292,6 +297,51 @@ def p2p_roofline(live, pk, lattice, info, bench_workload, passb_kernel):
     return roof
 
 
+def bnd_roofline(live, pk, lattice, info, w, hfmm, dev):
+    """Roofline object of the boundary operator's kernel (one launch = one
+    inner GMRES cycle of Pass B applies): algorithmic work per step = the
+    boundary -> boundary M2L (8 P^2 flop per cell pair) + the near field (23
+    flop-equivalents per point pair), counted by the library's stage counters
+    on a stage-chain apply of the same tree geometry; steps per launch = inner
+    steps of the timed solves / launches; time = CUDA events around every
+    launch (live, over the second pass of the K solves)."""
+    import torch
+    sm_, nl_, _ = live
+    os.environ["HFMM_BND_OP"] = "0"
+    try:
+        tc = hfmm.Tree(w["n"], w["k"], w["p"], w["theta"], w["leaf"], "fp32" if lattice else "fp64")
+    finally:
+        os.environ.pop("HFMM_BND_OP", None)
+    qb = torch.zeros(tc.n_bnd, dtype=torch.complex128, device=dev)
+    tc.set_timing(True)
+    tc.apply(None, qb, src=hfmm.SET_BND, tgt=hfmm.SET_BND)
+    torch.cuda.synchronize()
+    st = tc.stage_times()
+    tc.set_timing(False)
+    tc.close()
+    m2l_flop, p2p_pairs = st["m2l"][2], st["p2p"][2]
+    per_step = m2l_flop + P2P_FLOP_EQ_PER_PAIR * p2p_pairs
+    steps = info.inner_iters_total / max(1, info.iters)  # one cycle launch per outer iteration
+    per_launch_ms = sm_ / max(1, nl_)
+    work = per_step * steps
+    achieved = work / (per_launch_ms * 1e-3) / 1e12 if per_launch_ms > 0 else 0.0
+    peak = pk["fp32_tflops"] if lattice else pk["fp64_tflops"]
+    traffic = None
+    if BND_DRAM_BYTES is not None and lattice:
+        traffic = BND_DRAM_BYTES * steps / BND_DRAM_STEPS
+    return {"bound": "alu", "kernel": "k_bnd_op", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_kind": "measured",
+            "peak_source": ("FP32" if lattice else "FP64") + " FMA rate measured by hfmm_pipe_peaks",
+            "per_launch_ms": per_launch_ms, "work_per_launch": work, "steps_per_launch": steps,
+            "work_unit": f"flop-equivalents: 8 P^2 per M2L cell pair + {P2P_FLOP_EQ_PER_PAIR} per near-field "
+                         "point pair, boundary -> boundary, per inner step",
+            "m2l_flop_per_step": m2l_flop, "p2p_pairs_per_step": p2p_pairs,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one cycle launch of the "
+                               "benchmark solve, scaled by steps") if traffic is not None else None,
+            "source": "CUDA events around every launch of the kernel over a second pass of the K timed "
+                      "solves; the headline pass runs without them"}
+
+
 def p2p_per_pass(tree, hfmm, inputs, n, dev, pk, lattice, reps=10):
     """Near-field rate of each pass of the preconditioner (A: volume ->
     boundary, B: boundary -> boundary, C: all -> volume) from standalone
@@ -368,7 +418,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     stages = tree.stage_times()
     tree.set_timing(False)
-    dom = "p2p"  # the near-field kernel: the largest share of device time in the launch list
+    # the kernel with the largest share of device time in the launch list: the
+    # boundary operator's (the inner solves) when it serves Pass B, else the
+    # near field
+    dom = "bnd" if stages["bnd"][1] > 0 else "p2p"
     pk = hfmm.pipe_peaks()
 
     # the headline: K solves with no instrumentation
@@ -401,7 +454,7 @@ def run_ours(args, world, rank, local):
 
     # the roofline pass: the same K solves again, with CUDA events around
     # every launch of the near-field kernel (on the stream each launch uses)
-    tree.set_timing(True, stages=[dom])
+    tree.set_timing(True, stages=sorted({dom, "p2p"}))
     for _ in range(args.steps):
         flush.fill_(1.0)
         solve()
@@ -409,8 +462,9 @@ def run_ours(args, world, rank, local):
     live = tree.stage_times()
     tree.set_timing(False)
     lattice = args.precision == "fp32"
-    roof = p2p_roofline(live[dom], pk, lattice, info, args.workload == WORKLOAD, stages["bnd"][1] > 0)
-    roof["per_pass"] = p2p_per_pass(tree, hfmm, inputs, n, dev, pk, lattice)
+    roof_p2p = p2p_roofline(live["p2p"], pk, lattice, info, args.workload == WORKLOAD, stages["bnd"][1] > 0)
+    roof_p2p["per_pass"] = p2p_per_pass(tree, hfmm, inputs, n, dev, pk, lattice)
+    roof = bnd_roofline(live["bnd"], pk, lattice, info, w, hfmm, dev) if dom == "bnd" else roof_p2p
     stage_summary = {k: {"ms": v[0], "launches": v[1]} for k, v in stages.items()}
     # the far field's M2L stage over one fully timed solve (outside the timed
     # region): algorithmic 8 P^2 flop per cell pair over all its launches
@@ -648,7 +702,8 @@ def run_ours(args, world, rank, local):
             "solves_per_s": world / (ms * 1e-3),
             "fmm_apply_ms": app_ms, "fmm_apply_mpts_s": mpts,
             "gpu_launches": int(launches),
-            "roofline": roof, "roofline_m2l": roof_m2l, "stages_per_solve": stage_summary,
+            "roofline": roof, "roofline_p2p": roof_p2p if roof is not roof_p2p else None,
+            "roofline_m2l": roof_m2l, "stages_per_solve": stage_summary,
             "e2e": {"value": e2e_ms * 1e-3, "unit": "s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
             "fp64": fp64, "n128": big, "bicgstab": bicg, "batched": batched, "cpu_baseline": cpu, "clocks": clk,

@@ -92,6 +92,9 @@ struct BoArgs {
   // sorted indices of the panels of its near leaves
   const int* nsrc_ptr;
   const int* nsrc;
+  // items of SEG_NEAR: {leaf index, first and end panel within the leaf},
+  // the costliest first
+  const int4* near_items;
   int64_t tab_len;   // entries of the kernel table
   C<T>* nearv;       // [nb] near field + self term (SEG_NEAR)
   // tree arrays
@@ -418,10 +421,13 @@ __device__ __forceinline__ void bo_ns_get(const BoNs<double>& d, double2& q, int
 
 template <typename T, typename IO>
 __device__ void bo_near(const BoArgs<T, IO>& A, int idx, int leaf, C<T>* nearg, const C<T>* tab, BoNs<T>* ns_st,
-                        int g, int tg, int GT) {
+                        int g, int tg, int GT, int t0 = 0, int t1 = -1) {
   constexpr int TB = 6;
   const int lane = tg & 31, wg = tg >> 5, nwg = GT >> 5;
-  const int tlo = A.bfirst[leaf], nt = A.bfirst[leaf + 1] - tlo;
+  // panels [t0, t1) of the leaf (t1 < 0: all); nearg is indexed from the leaf's first panel
+  const int tall = A.bfirst[leaf + 1] - A.bfirst[leaf];
+  const int tlo = A.bfirst[leaf] + t0, nt = (t1 < 0 ? tall : t1) - t0;
+  nearg += t0;
   const int s0 = A.nsrc_ptr[idx], s1 = A.nsrc_ptr[idx + 1], nsrc = s1 - s0;
   const bool staged = ns_st && nsrc <= A.near_win;
   if (staged) {  // the leaf's sources into shared memory, in batches of loads
@@ -857,8 +863,9 @@ __device__ bool bo_apply_phases(const BoArgs<T, IO>& A, BoCta<T>& S, const C<T>*
               } else if (sg.type == SEG_ROWS) {
                 bo_rows_item<T, IO>(A, sg.level, i, gsm, g, tg, GT);
               } else {
-                const int leafc = A.act[A.loff[A.L] + i];
-                bo_near<T, IO>(A, i, leafc, A.nearv + A.bfirst[leafc], tab, ns_st, g, tg, GT);
+                const int4 it = A.near_items[i];
+                const int leafc = A.act[A.loff[A.L] + it.x];
+                bo_near<T, IO>(A, it.x, leafc, A.nearv + A.bfirst[leafc], tab, ns_st, g, tg, GT, it.y, it.z);
               }
               group_sync(g, GT);
               if (tg == 0) S.gnext[g] = (int)(nx - base);
@@ -1225,6 +1232,7 @@ struct bnd_op_state {
   int *nsrc_ptr = nullptr, *nsrc = nullptr;
   int2* rng = nullptr;
   int *pslot = nullptr, *crow = nullptr, *cpid = nullptr;
+  int4* near_items = nullptr;
   int near_win = 0;        // sources of a leaf's near field staged in shared memory (0: none)
   void* Rb = nullptr;     // basis rows of the boundary points, sorted order
   void* qb = nullptr;     // weights, sorted order
@@ -1339,12 +1347,14 @@ void bo_schedule(bnd_op_state* b, int L, int nact[], int chunk_first[], int chun
     --cur;
     plo = phi = cur;
   }
+  // the near field needs only the sorted weights (phase 0): from L = 4 on it
+  // runs after the first products, its items filling the groups that finish
+  // their products early
   const bool near_early = L >= 4;
+  if (near_early) phases[1].push_back(BoSeg{SEG_NEAR, L, 0, nact[L]});
   for (int l = (L == 2 ? 2 : 3); l <= L; ++l) {
     const int fl = (rows_pre[l] ? DOWN_ROWS_PRE : 0) | (l == L && near_early ? DOWN_NEAR_PRE : 0);
-    std::vector<BoSeg> ph{BoSeg{SEG_DOWN, l, fl, nact[l]}};
-    if (near_early && l == L - 1) ph.push_back(BoSeg{SEG_NEAR, L, 0, nact[L]});
-    phases.push_back(ph);
+    phases.push_back({BoSeg{SEG_DOWN, l, fl, nact[l]}});
   }
   b->nphase = (int)phases.size();
   for (size_t i = 0; i < phases.size(); ++i) {
@@ -1505,6 +1515,20 @@ int bo_plan(fmm_tree* t, bool fp32, cudaStream_t s) {
   b->nb = (int)t->n_bnd;
   b->nbl = nact[L];
   bo_schedule(b, L, nact, b->chunk_first, b->chunk_count);
+  // the near-field items (one per boundary leaf) costliest first: taken
+  // from the counter in that order, the last to finish are cheap ones
+  {
+    std::vector<std::pair<int64_t, int>> c(nact[L]);
+    for (int i = 0; i < nact[L]; ++i) {
+      const int leaf = act[t->level_off[L] + i];
+      c[i] = {-(int64_t)(bfirst[leaf + 1] - bfirst[leaf]) * (nsrc_ptr[i + 1] - nsrc_ptr[i]), i};
+    }
+    std::stable_sort(c.begin(), c.end(),
+                     [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) { return x.first < y.first; });
+    std::vector<int4> items(std::max(1, nact[L]), make_int4(0, 0, 0, 0));
+    for (int k = 0; k < nact[L]; ++k) items[k] = make_int4(c[k].second, 0, -1, 0);
+    HFMM_TRY(to_dev(t, &b->near_items, items));
+  }
   // launch shape: one CTA per SM, product groups sized to the shared memory
   const size_t csz = fp32 ? sizeof(float2) : sizeof(double2);
   // dynamic shared memory left beside the kernel's static arrays (at most 220 KB)
@@ -1605,6 +1629,7 @@ int bo_launch(fmm_tree* t, const IO* x, IO* y, double scale, cudaStream_t s, int
   A.tab = reinterpret_cast<const C<T>*>(sizeof(T) == 4 ? (const void*)t->lat_tab32 : (const void*)t->lat_tab64);
   A.nsrc_ptr = b->nsrc_ptr;
   A.nsrc = b->nsrc;
+  A.near_items = b->near_items;
   A.tab_len = t->lat_half;
   A.nearv = reinterpret_cast<C<T>*>(b->nearv);
   A.flags = t->flags;
