@@ -9,17 +9,21 @@
 // latency of its dependent loads.  Here the same stages run as phases of one
 // cooperative kernel whose CTAs stay resident (one per SM), separated by grid
 // barriers whose waits are bounded (about one second; on time-out the kernel
-// records HFMM_ERR_TIMEOUT and every CTA returns):
-//   phase 1   P2M at the boundary leaves, M2M into their parents (per parent)
-//   next      M2L products of the levels whose multipoles are complete: the
-//             (target, source) cell pairs grouped by operator slot, 32 per
-//             item, operator (bulk copy) and source rows (cp.async) double-
-//             buffered per group of threads; M2M one level further up
-//   next      M2L into level 2, summed directly per target cell; the near
-//             field through the lattice kernel table, with the self term
-//   then      per level l = 3 .. L: L_l = (sum of the cell's product rows in
-//             pair order) + L2L of its parent's L; at the leaf level L2P plus
-//             the near field, written to the output in the caller's order
+// records HFMM_ERR_TIMEOUT and every CTA returns).  For a leaf level L >= 4:
+//   phase 0   P2M at the boundary leaves, M2M into their parents (per parent)
+//   phase 1   M2L products of levels L-1 and L: the (target, source) cell
+//             pairs grouped by operator slot, 32 per item, operator (bulk
+//             copy) and source rows (TMA gathers) double-buffered per group
+//             of threads; M2M into level 2; then the near field of the
+//             leaves through the lattice kernel table, with the self term
+//   phase 2   products of level 2; row sums (pair order) of levels L-1, L
+//   then      per level l = 3 .. L: L_l = (its row sum) + L2L of its
+//             parent's L; at the leaf level L2P plus the near field, written
+//             to the output in the caller's order
+// (shallower trees fold the row sums and the near field into the downward
+// phases).  Inside the inner solve the kernel runs the whole GMRES cycle:
+// per step one apply as above, then classical Gram-Schmidt twice, the Givens
+// update, and at the end the back substitution and x = V y.
 // Every sum is taken in a fixed order, so results are deterministic.  Input
 // and output are boundary vectors in the caller's (original) panel order; the
 // kernel reads x through the sorted order itself.
@@ -48,7 +52,7 @@ constexpr int BO_CHUNK = 32;  // pairs per product item (the pair lists' chunk s
 // smaller CTAs keep more registers.
 __host__ __device__ constexpr int bo_fit(int R, int RT, int csz, int nst) {
   const int P = R * RT;  // largest P of the configuration
-  const int gbytes = nst * (P * P + 32 * (P + 2)) * csz;
+  const int gbytes = nst * (P * P + 32 * P) * csz;
   const int by_smem = (200 * 1024) / gbytes;
   const int by_thr = 512 / (RT * 8);
   const int n = by_smem < by_thr ? by_smem : by_thr;
@@ -96,6 +100,9 @@ struct BoArgs {
   // the costliest first
   const int4* near_items;
   int64_t tab_len;   // entries of the kernel table
+  // the multipoles M as a 2-D tensor (rows of 2P reals) for the TMA gathers
+  // of the product items' source rows
+  CUtensorMap mrows;
   C<T>* nearv;       // [nb] near field + self term (SEG_NEAR)
   // tree arrays
   const int* flags;
@@ -239,14 +246,7 @@ __device__ __forceinline__ C<T> weight(const BoArgs<T, IO>& A, int i) {
   return mkc<T>(A.scale * v.x, A.scale * v.y);
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa(dst)), "l"(src) : "memory");
-}
-// one arrival on the mbarrier once this thread's earlier cp.async copies have
-// landed (counted in the barrier's expected arrivals)
-__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(sa(bar)) : "memory");
-}
+
 // named barriers: 1 .. BO_MAX_NG for the thread groups of the product and
 // downward items, 8 and 9 for the two teams of the upward items
 __device__ __forceinline__ void group_sync(int g, int nthreads) {
@@ -614,7 +614,7 @@ template <typename T, typename IO, int R, int J, int RT>
 __device__ __forceinline__ void bo_prod_cols(const BoArgs<T, IO>& A, const C<T>* Ts, const C<T>* Ms,
                                              const int* pids, int cw, int r0, int c0) {
   constexpr int CT = 8;
-  const int P = A.P, MS = P + 2;
+  const int P = A.P, MS = P;
   int pid[J];
 #pragma unroll
   for (int q = 0; q < J; ++q) {
@@ -649,19 +649,20 @@ constexpr int BO_NBAR = 5;  // mbarriers per group: two stages, three record slo
 // group of GT = RT * 8 threads.  Every copy completes on an mbarrier: the
 // records of the item three ahead (bulk copies) into one of three record
 // slots, and for the item NST ahead the operator (one bulk copy) and the
-// source rows (16-byte cp.async by every thread of the group, from the
-// records, each thread arriving once when its copies have landed: stage
-// barriers expect 1 + GT arrivals) into one of NST stages, so that all
-// latencies overlap the products of the current item.  Every thread of the
-// group waits for each completion it reads (and all track the barriers'
-// phases alike).  Returns false on a wait time-out.
+// source rows (TMA gathers of four rows each, from the records, issued by
+// the first lanes of the group's first warp) into one of NST stages, so that
+// all latencies overlap the products of the current item.  Source rows sit
+// at a stride of P in a stage (4 P elements = 32 P or 64 P bytes, a multiple
+// of 128 for even p, so every gather lands on a 128-byte boundary).  Every
+// thread of the group waits for each completion it reads (and all track the
+// barriers' phases alike).  Returns false on a wait time-out.
 template <typename T, typename IO, int R, int CM, int RT>
 __device__ bool bo_products(const BoArgs<T, IO>& A, const BoSeg& sg, unsigned char* sm, uint64_t* mbar,
                             uint32_t& phase_bits, int* gabort, BoRec (*rec)[3]) {
   constexpr int GT = RT * 8, CT = 8, TC = CT * CM;
   static_assert(TC == BO_CHUNK, "one product column per pair of a chunk");
   static_assert(BO_NBAR * BO_MAX_NG <= 32, "phase bits of every group in one word");
-  const int P = A.P, MS = P + 2;
+  const int P = A.P, MS = P;
   const int g = threadIdx.x / GT, tg = threadIdx.x - g * GT;
   if (g >= A.ng) return true;
   const size_t op_elems = (size_t)P * P, ms_elems = (size_t)TC * MS;
@@ -692,28 +693,33 @@ __device__ bool bo_products(const BoArgs<T, IO>& A, const BoSeg& sg, unsigned ch
     }
     pending |= bit(2 + s);
   };
-  // operator and source rows of item j into stage j % NST (every thread
+  // operator and source rows of item j into stage j % NST (the first warp
   // waits for the records of item j without consuming that phase)
-  const int row16 = (int)(row_bytes / 16);
   auto stage_issue = [&](int j) {
     if (j >= nitems) return;
     const int st = j % NST, s = j % 3;
-    if (tc_wait(&bar[2 + s], par(2 + s))) {
-      C<T>* Ts = base + (size_t)st * (op_elems + ms_elems);
-      C<T>* Ms = Ts + op_elems;
-      const int4 ch = rec[g][s].ch;
-      if (tg == 0) {
-        tc_expect_tx(&bar[st], op_bytes);
-        tc_bulk_g2s(Ts, A.m2l + ((int64_t)ch.x * A.box_cells + ch.y) * P * P, op_bytes, &bar[st]);
+    if (tg < 32) {
+      const bool ok = tc_wait(&bar[2 + s], par(2 + s));
+      if (__all_sync(0xffffffffu, ok)) {
+        C<T>* Ts = base + (size_t)st * (op_elems + ms_elems);
+        C<T>* Ms = Ts + op_elems;
+        const int4 ch = rec[g][s].ch;
+        const int ngath = (ch.w + 3) >> 2;
+        if (tg == 0) {
+          tc_expect_tx(&bar[st], op_bytes + (uint32_t)ngath * 4u * row_bytes);
+          tc_bulk_g2s(Ts, A.m2l + ((int64_t)ch.x * A.box_cells + ch.y) * P * P, op_bytes, &bar[st]);
+        }
+        __syncwarp();
+        if (tg < ngath) {
+          // rows past the chunk's width repeat its last row (never stored)
+          const int* rw = rec[g][s].row;
+          const int c0 = 4 * tg, last = ch.w - 1;
+          tc_gather4(Ms + (size_t)c0 * MS, &A.mrows, 0, rw[c0], rw[min(c0 + 1, last)], rw[min(c0 + 2, last)],
+                     rw[min(c0 + 3, last)], &bar[st]);
+        }
+      } else if (tg == 0) {
+        fail();
       }
-      for (int e = tg; e < ch.w * row16; e += GT) {
-        const int c = e / row16, pc = e - c * row16;
-        cp_async16(reinterpret_cast<unsigned char*>(Ms + (size_t)c * MS) + 16 * pc,
-                   reinterpret_cast<const unsigned char*>(A.M + (int64_t)rec[g][s].row[c] * P) + 16 * pc);
-      }
-      cp_async_arrive_noinc(&bar[st]);
-    } else {
-      fail();
     }
     pending |= bit(st);
   };
@@ -1205,9 +1211,9 @@ __global__ void __launch_bounds__(RT * 8 * bo_groups(R, RT, (int)sizeof(C<T>)), 
   __shared__ int gnext[BO_MAX_NG];
   __shared__ int cbt[2][9];
   if (threadIdx.x == 0) {
-    // per group: two stage barriers (the operator's expect-tx arrival and
-    // one cp.async arrival per thread of the group), three record slots
-    for (int i = 0; i < BO_NBAR * BO_MAX_NG; ++i) tc_mbar_init(&mbar[i], (i % BO_NBAR) < 2 ? 1 + RT * 8 : 1);
+    // per group: two stage barriers, three record slots (one expect-tx
+    // arrival each)
+    for (int i = 0; i < BO_NBAR * BO_MAX_NG; ++i) tc_mbar_init(&mbar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int i = 0; i < BO_MAX_NG; ++i) gabort[i] = 0;
   }
@@ -1233,6 +1239,7 @@ struct bnd_op_state {
   int2* rng = nullptr;
   int *pslot = nullptr, *crow = nullptr, *cpid = nullptr;
   int4* near_items = nullptr;
+  CUtensorMap mrows;       // the tree's multipoles as rows of 2P reals (TMA gathers)
   int near_win = 0;        // sources of a leaf's near field staged in shared memory (0: none)
   void* Rb = nullptr;     // basis rows of the boundary points, sorted order
   void* qb = nullptr;     // weights, sorted order
@@ -1501,6 +1508,20 @@ int bo_plan(fmm_tree* t, bool fp32, cudaStream_t s) {
   HFMM_TRY(tree_alloc(t, &b->qb, cs * (size_t)t->n_bnd));
   HFMM_TRY(tree_alloc(t, &b->nearv, cs * (size_t)t->n_bnd));
   HFMM_TRY(tree_alloc(t, &b->Rb, cs * (size_t)t->n_bnd * P));
+  {
+    // M [total_cells][P] complex as a 2-D tensor of rows of 2P reals, box one
+    // row high (the products gather their source rows four at a time)
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || 2 * P > 256) return HFMM_ERR_UNSUPPORTED;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * P), (cuuint64_t)t->total_cells};
+    const cuuint64_t strides[1] = {(cuuint64_t)(2 * P) * (fp32 ? 4u : 8u)};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * P), 1u};
+    const cuuint32_t es[2] = {1u, 1u};
+    if (enc(&b->mrows, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, t->M, dims, strides,
+            box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return HFMM_ERR_UNSUPPORTED;
+  }
   const int64_t nrow = t->n_bnd * (int64_t)P;
   if (fp32)
     k_bo_rows<float><<<ceil_div(nrow, 256), 256, 0, s>>>(t->n_bnd, P, d_bsort, (const float2*)t->rtab, (float2*)b->Rb);
@@ -1547,7 +1568,7 @@ int bo_plan(fmm_tree* t, bool fp32, cudaStream_t s) {
     smem_cap = std::min(smem_cap, (size_t)optin - stat);
   }
   const int nst = bo_stages(cfg.R, cfg.RT, (int)csz);
-  const size_t group_bytes = (size_t)nst * ((size_t)P * P + (size_t)BO_CHUNK * (P + 2)) * csz;
+  const size_t group_bytes = (size_t)nst * ((size_t)P * P + (size_t)BO_CHUNK * P) * csz;
   const size_t budget = std::min<size_t>(200 * 1024, smem_cap);
   const int GT = cfg.RT * 8;
   int ng = (int)std::min<size_t>(std::min(BO_MAX_NG, 512 / GT), budget / group_bytes);
@@ -1630,6 +1651,7 @@ int bo_launch(fmm_tree* t, const IO* x, IO* y, double scale, cudaStream_t s, int
   A.nsrc_ptr = b->nsrc_ptr;
   A.nsrc = b->nsrc;
   A.near_items = b->near_items;
+  A.mrows = b->mrows;
   A.tab_len = t->lat_half;
   A.nearv = reinterpret_cast<C<T>*>(b->nearv);
   A.flags = t->flags;
