@@ -64,7 +64,7 @@ P2P_DRAM_BYTES = {"A": 2617088, "B": 520704, "C": 5694976}
 # The boundary operator's kernel (k_bnd_op, one launch = one inner GMRES
 # cycle): dram__bytes_read.sum + dram__bytes_write.sum of one such launch in
 # the benchmark solve (ncu, 64^3 k=16 p=6 FP32, 20 steps), and its steps
-BND_DRAM_BYTES = None
+BND_DRAM_BYTES = 235075584
 BND_DRAM_STEPS = 20
 L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
 

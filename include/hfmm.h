@@ -380,8 +380,9 @@ int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_x, int coun
  * FMM passes of the preconditioner and on the full apply, then, with the
  * chosen M2L, the tile shapes of the lattice near field (tiled 4 x 4
  * target-source groups or not in the FP32 form; at most 8, 16 or 32 threads
- * per group of targets; one block per SM or as many as fit), and keeps the
- * fastest per pass in the handle.  The choice changes only the order in
+ * per group of targets; one block per SM or as many as fit) and whether the
+ * near field runs on a side stream concurrently with the far field, and keeps
+ * the fastest per pass in the handle.  The choice changes only the order in
  * which contributions are summed (rounding-level differences); a handle's
  * results stay deterministic.  Also tunes the handle's inner-order tree
  * (fmm_set_inner_order) when it has one.

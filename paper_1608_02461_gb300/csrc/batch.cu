@@ -12,8 +12,9 @@
 // (grid filled to 1, 2, 4 or 8 times the SM count) on the FMM passes the
 // preconditioner uses, then, with that M2L, the shapes of the lattice near
 // field (tiled 4 x 4 target-source groups or not, at most 8, 16 or 32
-// threads per target group, one block per SM or as many as fit), and keeps
-// the fastest per pass in the handle.
+// threads per target group, one block per SM or as many as fit) and whether
+// the near field runs concurrently with the far field, and keeps the fastest
+// per pass in the handle.
 #include <algorithm>
 #include <atomic>
 #include <thread>
@@ -109,6 +110,24 @@ extern "C" int fmm_autotune(fmm_tree* t, void* stream) {
     t->tuned_p2p_tile[ci] = btile;
     t->tuned_p2p_tpt[ci] = btpt;
     t->tuned_p2p_blocks[ci] = bblk;
+    // near field concurrent with the far field or after it
+    if (!t->overlap_near || !t->near_stream || !t->phis_near) continue;
+    best = 1e30f;
+    int bov = -1;
+    for (int ov = 0; ov < 2; ++ov) {
+      t->tuned_overlap[ci] = ov;
+      float ms = 0.f;
+      int st = time_core(t, src, tgt, s, 3, &ms);
+      if (st != HFMM_OK) {
+        t->timer.on = timer_was_on;
+        return st;
+      }
+      if (ms < best) {
+        best = ms;
+        bov = ov;
+      }
+    }
+    t->tuned_overlap[ci] = bov;
   }
   t->timer.on = timer_was_on;
   if (t->inner) return fmm_autotune(t->inner, stream);  // the inner solve's tree

@@ -2551,12 +2551,13 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s, bool dipole
   (void)nleaf;
 
   StageTimer& tm = t->timer;
-  // near field on its own stream, concurrent with the far-field chain, when
-  // the targets are the boundary points: there the far-field kernels are
-  // small and latency-bound and leave most SMs idle (with volume targets both
-  // chains are compute-bound and running them together is slower)
-  const bool overlap =
-      !dipole && t->overlap_near && t->near_stream && t->phis_near && !(tgt_set & HFMM_SET_VOL);
+  // near field on its own stream, concurrent with the far-field chain, by
+  // default when the targets are the boundary points: there the far-field
+  // kernels are small and latency-bound and leave most SMs idle (with volume
+  // targets both chains are compute-bound); fmm_autotune may choose per pass
+  const int oci = 3 * (tgt_set - 1) + (src_set - 1);
+  const bool ov_pass = t->tuned_overlap[oci] >= 0 ? t->tuned_overlap[oci] != 0 : !(tgt_set & HFMM_SET_VOL);
+  const bool overlap = !dipole && t->overlap_near && t->near_stream && t->phis_near && ov_pass;
   if (overlap) {
     d.near = reinterpret_cast<C<T>*>(t->phis_near);
     cudaStream_t sn = t->near_stream;

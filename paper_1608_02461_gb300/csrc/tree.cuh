@@ -200,6 +200,10 @@ struct fmm_tree {
   int tuned_p2p_tile[9] = {};
   int tuned_p2p_tpt[9] = {};
   int tuned_p2p_blocks[9] = {};
+  // near field concurrent with the far field (1) or after L2P (0) per pass,
+  // same index; -1: not tuned (concurrent exactly when the targets are the
+  // boundary points)
+  int tuned_overlap[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
 
   // ---- near-field kernel table of lattice trees: every point is a node of
   //      the lattice h Z^3, so the kernel between two points depends only on
