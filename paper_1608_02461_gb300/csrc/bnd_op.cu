@@ -40,8 +40,11 @@ namespace {
 
 enum BoSegType { SEG_P2M_UP = 0, SEG_P2M = 1, SEG_M2M = 2, SEG_PROD = 3, SEG_DOWN = 4, SEG_ROWS = 5, SEG_NEAR = 6 };
 // SEG_DOWN flags (in BoSeg::first): the cell's product rows were summed into
-// its L by an earlier SEG_ROWS phase; the leaves' near field is in nearv
-constexpr int DOWN_ROWS_PRE = 1, DOWN_NEAR_PRE = 2;
+// its L by an earlier SEG_ROWS phase; the leaves' near field is in nearv;
+// the leaf item computes its parent's L itself (the parent's rows summed
+// earlier, plus L2L of the grandparent's L: its rows at level 2, else Lc), so
+// that no downward phase of level L - 1 is needed
+constexpr int DOWN_ROWS_PRE = 1, DOWN_NEAR_PRE = 2, DOWN_PARENT = 4;
 constexpr int BO_MAX_PH = 12, BO_MAX_SEG = 4, BO_MAX_NG = 5;
 constexpr int BO_CHUNK = 32;  // pairs per product item (the pair lists' chunk size)
 
@@ -555,11 +558,36 @@ __device__ void bo_down(const BoArgs<T, IO>& A, int level, int idx, int flags, C
   } else {
     bo_rows<T, IO>(A, A.rng[A.loff[level] + cell], part, tg, S);
   }
-  if (level == 3) bo_rows<T, IO>(A, A.rng[A.loff[2] + parent], pp, tg, S);
-  else if (level > 3)
+  if (flags & DOWN_PARENT) {
+    // the parent's L: its row sum (Lc, from an earlier row-sum phase) plus
+    // L2L of the grandparent's L (into Lv as scratch)
+    const int pl = level - 1, gp = parent >> 3, op = parent & 7;
+    if (pl - 1 == 2) bo_rows<T, IO>(A, A.rng[A.loff[2] + gp], pp, tg, S);
+    else
+      for (int a = tg; a < P; a += GT) Lv[a] = ldcg<T>(A.Lc + (A.loff[pl - 1] + gp) * P + a);
+    group_sync(g, GT);
+    if (pl - 1 == 2) {
+      for (int a = tg; a < P; a += GT) {
+        C<T> v = mkc<T>(0, 0);
+        for (int sp = 0; sp < S; ++sp) v = cadd<T>(v, pp[sp * P + a]);
+        Lv[a] = v;
+      }
+      group_sync(g, GT);
+    }
+    for (int ap = tg; ap < P; ap += GT) {
+      C<T> acc = ldcg<T>(A.Lc + (A.loff[pl] + parent) * P + ap);
+      const C<T>* Tc = A.l2l + ((int64_t)(pl - 1) * 8 + op) * P * P + ap;
+#pragma unroll 12
+      for (int a = 0; a < P; ++a) cfma<T>(acc, __ldg(Tc + (int64_t)a * P), Lv[a]);
+      Lp[ap] = acc;
+    }
+  } else if (level == 3) {
+    bo_rows<T, IO>(A, A.rng[A.loff[2] + parent], pp, tg, S);
+  } else if (level > 3) {
     for (int a = tg; a < P; a += GT) Lp[a] = ldcg<T>(A.Lc + (A.loff[level - 1] + parent) * P + a);
+  }
   group_sync(g, GT);
-  if (level == 3) {
+  if (level == 3 && !(flags & DOWN_PARENT)) {
     for (int a = tg; a < P; a += GT) {
       C<T> v = mkc<T>(0, 0);
       for (int sp = 0; sp < S; ++sp) v = cadd<T>(v, pp[sp * P + a]);
@@ -1359,8 +1387,13 @@ void bo_schedule(bnd_op_state* b, int L, int nact[], int chunk_first[], int chun
   // their products early
   const bool near_early = L >= 4;
   if (near_early) phases[1].push_back(BoSeg{SEG_NEAR, L, 0, nact[L]});
+  // from L = 4 on, with the rows of level L - 1 summed already, the leaves
+  // compute their parents' L themselves: no downward phase for level L - 1
+  const bool fold = near_early && rows_pre[L - 1];
   for (int l = (L == 2 ? 2 : 3); l <= L; ++l) {
-    const int fl = (rows_pre[l] ? DOWN_ROWS_PRE : 0) | (l == L && near_early ? DOWN_NEAR_PRE : 0);
+    if (fold && l == L - 1) continue;
+    const int fl = (rows_pre[l] ? DOWN_ROWS_PRE : 0) | (l == L && near_early ? DOWN_NEAR_PRE : 0) |
+                   (l == L && fold ? DOWN_PARENT : 0);
     phases.push_back({BoSeg{SEG_DOWN, l, fl, nact[l]}});
   }
   b->nphase = (int)phases.size();
