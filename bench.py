@@ -307,11 +307,15 @@ def bnd_roofline(live, pk, lattice, info, w, hfmm, dev):
     launch (live, over the second pass of the K solves)."""
     import torch
     sm_, nl_, _ = live
-    os.environ["HFMM_BND_OP"] = "0"
+    old = os.environ.get("HFMM_BND_OP")
+    os.environ["HFMM_BND_OP"] = "0"  # the stage chain counts the work of each stage
     try:
         tc = hfmm.Tree(w["n"], w["k"], w["p"], w["theta"], w["leaf"], "fp32" if lattice else "fp64")
     finally:
-        os.environ.pop("HFMM_BND_OP", None)
+        if old is None:
+            os.environ.pop("HFMM_BND_OP", None)
+        else:
+            os.environ["HFMM_BND_OP"] = old
     qb = torch.zeros(tc.n_bnd, dtype=torch.complex128, device=dev)
     tc.set_timing(True)
     tc.apply(None, qb, src=hfmm.SET_BND, tgt=hfmm.SET_BND)

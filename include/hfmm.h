@@ -300,8 +300,9 @@ int hfmm_order_for_k(double k, int p_min);
  *   *d_out = Re sum_i conj(g_i) (dG~/dk q)_i,   g = dL/dphi
  * (PyTorch's convention for complex tensors).  The tangent apply (HFMM_DK)
  * writes into device memory held by the handle (n_vol complex128, allocated
- * on the first call); the sum runs on the device in FP64 in a fixed order
- * (bit-identical on repeated calls).
+ * on the first call, so the first call must not be inside a stream capture);
+ * the sum runs on the device in FP64 in a fixed order (bit-identical on
+ * repeated calls).
  *   d_q_vol, d_g_vol  n_vol complex128 (device), read only
  *   d_out             one double (device), overwritten
  * Errors: INVALID_ARG (null pointer, no volume points), NOMEM, CUDA.
@@ -313,7 +314,8 @@ int fmm_grad_k(fmm_tree* tree, const void* d_q_vol, const void* d_g_vol, double*
  * x = A(k)^-1 b of the 7-point system (Sec. 2).  For real k, A is real and
  * symmetric with dA/dk = -2k I, so with lam the solution of A lam = dL/dx:
  *   *d_out = -Re <lam, (dA/dk) x> = 2k Re sum_i conj(lam_i) x_i
- * summed on the device in FP64 in a fixed order.
+ * summed on the device in FP64 in a fixed order (scratch held by the handle,
+ * allocated on the first call of either gradient entry point).
  *   d_lam, d_x  n^3 complex128 (device), read only
  *   d_out       one double (device), overwritten
  * Lattice trees only (UNSUPPORTED otherwise).  Errors: INVALID_ARG, NOMEM, CUDA.
