@@ -162,6 +162,7 @@ void release(fmm_tree* t) {
   t->near_stream = nullptr;
   t->timer.destroy();
   m2l_tc_release(t);
+  near_tc_release(t);
   bnd_op_release(t);
   if (t->gaunt) cudaFree(t->gaunt);
   t->gaunt = nullptr;
@@ -243,6 +244,7 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   if (const char* v = getenv("HFMM_BASIS_TABLE")) t->use_rtab = atoi(v) != 0;
   if (const char* v = getenv("HFMM_OVERLAP_NEAR")) t->overlap_near = atoi(v) != 0;
   if (const char* v = getenv("HFMM_M2L_TC")) t->use_m2l_tcore = atoi(v);
+  if (const char* v = getenv("HFMM_NEAR_TC")) t->use_near_tcore = atoi(v);
   if (const char* v = getenv("HFMM_BND_OP")) t->use_bnd_op = atoi(v);
   // 1 (default): the one-kernel boundary operator where it was measured
   // faster than the stage chain (up to p = 6; at p = 8 the products are

@@ -2557,7 +2557,10 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s, bool dipole
   // targets both chains are compute-bound); fmm_autotune may choose per pass
   const int oci = 3 * (tgt_set - 1) + (src_set - 1);
   const bool ov_pass = t->tuned_overlap[oci] >= 0 ? t->tuned_overlap[oci] != 0 : !(tgt_set & HFMM_SET_VOL);
-  const bool overlap = !dipole && t->overlap_near && t->near_stream && t->phis_near && ov_pass;
+  // volume targets of a regular lattice: the volume sources' near field as
+  // dense blocks on the tensor cores, after L2P (adding into phis)
+  const bool near_tc = !dipole && near_tc_usable(t, src_set, tgt_set, s);
+  const bool overlap = !dipole && !near_tc && t->overlap_near && t->near_stream && t->phis_near && ov_pass;
   if (overlap) {
     d.near = reinterpret_cast<C<T>*>(t->phis_near);
     cudaStream_t sn = t->near_stream;
@@ -2612,11 +2615,20 @@ int core_impl(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s, bool dipole
   tm.end(1, s);
   if (!overlap) {
     tm.begin(HFMM_STAGE_P2P, s);
-    if (dipole)
+    int nl = 1;
+    if (dipole) {
       HFMM_TRY(p2p_stage<T, 3>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));
-    else
+    } else if (near_tc) {
+      HFMM_TRY(near_tc_stage(t, s, &nl));
+      count_launches(nl);
+      if (src_set & HFMM_SET_BND) {
+        HFMM_TRY(p2p_stage<T, 0>(t, d, HFMM_SET_BND, tgt_set, t->sigma_vol, t->sigma_bnd, s));
+        ++nl;
+      }
+    } else {
       HFMM_TRY(p2p_stage<T, 0>(t, d, src_set, tgt_set, t->sigma_vol, t->sigma_bnd, s));
-    tm.end(1, s, tm.on ? p2p_work(t, src_set, tgt_set) : 0.0);
+    }
+    tm.end(nl, s, tm.on ? p2p_work(t, src_set, tgt_set) : 0.0);
   }
   count_launches(2);
   return hfmm_last_launch();

@@ -38,6 +38,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "tc.cuh"
 #include "tree.cuh"
@@ -357,6 +358,88 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(const __grid_constant_
   }
 }
 
+// ---- the volume -> volume near field of a regular lattice tree on the
+// tensor cores.  When every leaf holds the same s x s x s block of lattice
+// nodes (n divisible by 2^L), the kernel block between the nodes of a target
+// leaf and those of a source leaf at leaf offset o depends only on o: K_o(t,
+// j) = G(h (s o + x_j - x_t)), the same for every leaf pair.  The near field
+// of the volume targets from the volume sources is then, per near offset, the
+// product of that fixed npl x npl matrix with the weights of the shifted leaf:
+// the M2L's structure with the leaf's weights for its multipole and K_o for
+// its operator, so the tensor-core M2L kernel computes it unchanged.
+
+// operator images of the near offsets: slot i = near offset i, B^T[n][k] of
+// K_o in the real form of the M2L images (n = 2t + c', k = 2j + c), read from
+// the lattice table through the codes of a reference leaf and its neighbour
+__global__ void k_tc_near_ops(const float2* __restrict__ tab, const int* __restrict__ lin, int ref_first,
+                              const int* __restrict__ src_first, int nslot, int npl, int NA, int Npad,
+                              float* __restrict__ img) {
+  const int64_t per_slot = (int64_t)2 * NA * Npad * 32;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nslot * NA * Npad * 32) return;
+  const int sl = (int)(e / ((int64_t)NA * Npad * 32));
+  int64_t r = e - (int64_t)sl * NA * Npad * 32;
+  const int a = (int)(r / (Npad * 32));
+  r -= (int64_t)a * Npad * 32;
+  const int n = (int)(r / 32), kk = (int)(r % 32);
+  const int k = 32 * a + kk;
+  float v = 0.f;
+  if (n < 2 * npl && k < 2 * npl) {
+    const int t = n >> 1, cp = n & 1, j = k >> 1, ci = k & 1;
+    const int dl = lin[ref_first + t] - lin[src_first[sl] + j];
+    const float2 T = tab[dl < 0 ? -dl : dl];
+    v = (cp == ci) ? T.x : (cp == 0 ? -T.y : T.y);
+  }
+  const float hv = tf32_hi(v);
+  const int64_t pos = (int64_t)n * 32 + (((kk >> 2) ^ (n & 7)) << 2) + (kk & 3);
+  float* base = img + sl * per_slot + (int64_t)a * Npad * 32;
+  base[pos] = hv;
+  base[(int64_t)NA * Npad * 32 + pos] = v - hv;
+}
+
+// X_hi / X_lo of the leaf level from the sorted weights: the row of leaf m is
+// its npl volume weights (2 npl reals), zero for leaves without volume points
+__global__ void k_tc_near_split(const float2* __restrict__ qs, const int* __restrict__ leaf_start,
+                                const int* __restrict__ flags, int64_t off, int l, int npl,
+                                float* __restrict__ xh, float* __restrict__ xl, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t ncell = (int64_t)1 << (3 * l);
+  const int twoP = 2 * npl;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ncell * twoP) return;
+  const int64_t m = e / twoP;
+  const int k = (int)(e - m * twoP);
+  int ix, iy, iz;
+  morton_decode((uint64_t)m, ix, iy, iz);
+  const int h = 1 << (l - 1);
+  const int c = (ix & 1) | ((iy & 1) << 1) | ((iz & 1) << 2);
+  const int64_t row = (((int64_t)c * h + (iz >> 1)) * h + (iy >> 1)) * h + (ix >> 1);
+  float v = 0.f;
+  if (flags[off + m] & HFMM_SET_VOL) {
+    const float2 q = qs[leaf_start[m] + (k >> 1)];
+    v = (k & 1) ? q.y : q.x;
+  }
+  const float hv = tf32_hi(v);
+  xh[row * twoP + k] = hv;
+  xl[row * twoP + k] = v - hv;
+}
+
+// phis += near field + self term, for the volume points of every leaf
+__global__ void k_tc_near_add(const float* __restrict__ out, int64_t off, const int* __restrict__ leaf_start,
+                              const int* __restrict__ flags, int64_t nleaf, int npl, float2 sig,
+                              const float2* __restrict__ qs, float2* __restrict__ phis, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nleaf * npl) return;
+  const int64_t m = e / npl;
+  const int t = (int)(e - m * npl);
+  if (!(flags[off + m] & HFMM_SET_VOL)) return;
+  const int j = leaf_start[m] + t;
+  const float* o = out + (off + m) * 2 * npl + 2 * t;
+  const float2 q = qs[j], p = phis[j];
+  phis[j] = make_float2(p.x + o[0] + (sig.x * q.x - sig.y * q.y), p.y + o[1] + (sig.x * q.y + sig.y * q.x));
+}
+
 // L = (L +) sum over splits of the partial rows, for the target cells of the
 // tensor-core levels
 __global__ void k_tc_reduce(const float* __restrict__ part, int64_t part_stride, int nsplit,
@@ -516,4 +599,189 @@ int m2l_tc_error(cudaStream_t s, bool clear) {
     cudaMemcpyToSymbolAsync(g_tc_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s);
   }
   return h;
+}
+
+// ---------------------------------------------------------------- near field on the tensor cores
+
+struct fmm_tc_near_state {
+  int ok = 0;        // 1 usable, -1 not for this tree
+  int npl = 0, NA = 0, Npad = 0;
+  float* img = nullptr;
+  float* xh = nullptr;
+  float* xl = nullptr;
+  float* out = nullptr;   // [level_off[L] + 8^L][2 npl] (rows of the leaf level used)
+  float* part = nullptr;  // [TC_NEAR_SPLIT][level_off[L] + 8^L][2 npl]
+  int* offs = nullptr;    // [8][near_count] packed near offsets (every class the same list)
+  int* slots = nullptr;   // [8][near_count] slot = offset index
+  TcMaps maps;
+};
+
+namespace {
+constexpr int TC_NEAR_SPLIT = 16;
+}
+
+void near_tc_release(fmm_tree* t) {
+  delete t->near_tcore;  // device buffers belong to the handle's allocation list
+  t->near_tcore = nullptr;
+}
+
+// eligibility and set-up (host, once per tree): FP32 lattice tree of depth
+// >= 4 whose leaves all hold the same s x s x s block of nodes (checked on the
+// lattice codes of every leaf against a reference leaf), npl = s^3 <= 128
+static int near_tc_prepare(fmm_tree* t, cudaStream_t s) {
+  if (t->near_tcore) return t->near_tcore->ok > 0 ? HFMM_OK : HFMM_ERR_UNSUPPORTED;
+  fmm_tc_near_state* S = new (std::nothrow) fmm_tc_near_state();
+  if (!S) return HFMM_ERR_NOMEM;
+  t->near_tcore = S;
+  S->ok = -1;
+  const int L = t->L;
+  if (!t->lattice || t->precision != HFMM_FP32 || L < 4 || !t->lat_D || !t->lat_tab32 || t->near_count > TC_MAX_COUNT ||
+      t->n % (1 << L))
+    return HFMM_ERR_UNSUPPORTED;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return HFMM_ERR_UNSUPPORTED;
+  const int sn = t->n >> L, npl = sn * sn * sn;
+  if (2 * npl > TC_MAX_NPAD) return HFMM_ERR_UNSUPPORTED;
+  const int64_t nleaf = (int64_t)1 << (3 * L);
+  std::vector<int> ls(nleaf + 1), lm(nleaf), lin(t->n_pts);
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  HFMM_CUDA_TRY(cudaMemcpy(ls.data(), t->leaf_start, sizeof(int) * (nleaf + 1), cudaMemcpyDeviceToHost));
+  HFMM_CUDA_TRY(cudaMemcpy(lm.data(), t->leaf_mid, sizeof(int) * nleaf, cudaMemcpyDeviceToHost));
+  HFMM_CUDA_TRY(cudaMemcpy(lin.data(), t->lat_lin, sizeof(int) * t->n_pts, cudaMemcpyDeviceToHost));
+  // every leaf: npl volume points, whose codes are the reference leaf's
+  // shifted by one constant (the same node pattern)
+  const int half = 1 << (L - 1);
+  const int64_t ref = (int64_t)morton_encode(half, half, half);
+  for (int64_t m = 0; m < nleaf; ++m) {
+    if (lm[m] - ls[m] != npl) return HFMM_ERR_UNSUPPORTED;
+    const int sh = lin[ls[m]] - lin[ls[ref]];
+    for (int q = 1; q < npl; ++q)
+      if (lin[ls[m] + q] - lin[ls[ref] + q] != sh) return HFMM_ERR_UNSUPPORTED;
+  }
+  // the reference leaf's near neighbours (all inside the level)
+  std::vector<int> noff(t->near_count), src_first(t->near_count);
+  HFMM_CUDA_TRY(cudaMemcpy(noff.data(), t->near_off, sizeof(int) * t->near_count, cudaMemcpyDeviceToHost));
+  const int sl = 1 << L;
+  for (int i = 0; i < t->near_count; ++i) {
+    const int o = noff[i];
+    const int jx = half + (o & 255) - 128, jy = half + ((o >> 8) & 255) - 128, jz = half + ((o >> 16) & 255) - 128;
+    if (jx < 0 || jy < 0 || jz < 0 || jx >= sl || jy >= sl || jz >= sl) return HFMM_ERR_UNSUPPORTED;
+    src_first[i] = ls[morton_encode(jx, jy, jz)];
+  }
+  S->npl = npl;
+  const int twoP = 2 * npl;
+  S->NA = (twoP + 31) / 32;
+  S->Npad = (twoP + 15) / 16 * 16;
+  const int nslot = t->near_count;
+  std::vector<int> offs(8 * (size_t)nslot), slots(8 * (size_t)nslot);
+  for (int c = 0; c < 8; ++c)
+    for (int i = 0; i < nslot; ++i) {
+      offs[(size_t)c * nslot + i] = noff[i];
+      slots[(size_t)c * nslot + i] = i;
+    }
+  int* d_src_first = nullptr;
+  HFMM_TRY(tree_alloc(t, (void**)&d_src_first, sizeof(int) * nslot));
+  HFMM_TRY(tree_alloc(t, (void**)&S->offs, sizeof(int) * offs.size()));
+  HFMM_TRY(tree_alloc(t, (void**)&S->slots, sizeof(int) * slots.size()));
+  HFMM_CUDA_TRY(cudaMemcpy(d_src_first, src_first.data(), sizeof(int) * nslot, cudaMemcpyHostToDevice));
+  HFMM_CUDA_TRY(cudaMemcpy(S->offs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice));
+  HFMM_CUDA_TRY(cudaMemcpy(S->slots, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice));
+  const int64_t img_floats = (int64_t)nslot * 2 * S->NA * S->Npad * 32;
+  HFMM_TRY(tree_alloc(t, (void**)&S->img, sizeof(float) * img_floats));
+  const int64_t nel = (int64_t)nslot * S->NA * S->Npad * 32;
+  k_tc_near_ops<<<ceil_div(nel, 256), 256, 0, s>>>(t->lat_tab32, t->lat_lin, ls[ref], d_src_first, nslot, npl, S->NA,
+                                                   S->Npad, S->img);
+  count_launches(1);
+  HFMM_TRY(hfmm_last_launch());
+  const int64_t rows = t->level_off[L] + nleaf;
+  HFMM_TRY(tree_alloc(t, (void**)&S->xh, sizeof(float) * nleaf * twoP));
+  HFMM_TRY(tree_alloc(t, (void**)&S->xl, sizeof(float) * nleaf * twoP));
+  HFMM_TRY(tree_alloc(t, (void**)&S->out, sizeof(float) * rows * twoP));
+  HFMM_TRY(tree_alloc(t, (void**)&S->part, sizeof(float) * rows * twoP * TC_NEAR_SPLIT));
+  const cuuint64_t hh = (cuuint64_t)half;
+  const cuuint64_t dims[5] = {(cuuint64_t)twoP, hh, hh, hh, 8};
+  const cuuint64_t row = (cuuint64_t)twoP * sizeof(float);
+  const cuuint64_t strides[4] = {row, row * hh, row * hh * hh, row * hh * hh * hh};
+  const cuuint32_t box[5] = {32, BX, BY, NBRK * BZ, 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  for (int w = 0; w < 2; ++w) {
+    CUresult r = enc(w ? &S->maps.xl[L] : &S->maps.xh[L], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, w ? S->xl : S->xh, dims,
+                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return HFMM_ERR_UNSUPPORTED;
+  }
+  HFMM_CUDA_TRY(cudaStreamSynchronize(s));
+  S->ok = 1;
+  return HFMM_OK;
+}
+
+bool near_tc_usable(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s) {
+  if (!t->use_near_tcore || t->precision != HFMM_FP32 || tgt_set != HFMM_SET_VOL || !(src_set & HFMM_SET_VOL))
+    return false;
+  if (!t->near_tcore) {
+    // set up on first use, outside any capture only
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      return false;
+    }
+    const int st = near_tc_prepare(t, s);
+    if (st != HFMM_OK && st != HFMM_ERR_UNSUPPORTED) return false;
+  }
+  return t->near_tcore && t->near_tcore->ok > 0;
+}
+
+// phis += the volume -> volume near field and the volume self terms (the
+// boundary sources' near field is left to the caller); *nlaunch = kernels
+int near_tc_stage(fmm_tree* t, cudaStream_t s, int* nlaunch) {
+  *nlaunch = 0;
+  HFMM_TRY(near_tc_prepare(t, s));
+  fmm_tc_near_state& S = *t->near_tcore;
+  const int L = t->L, npl = S.npl, twoP = 2 * npl;
+  const int64_t nleaf = (int64_t)1 << (3 * L);
+  const int64_t n = nleaf * twoP;
+  k_tc_near_split<<<ceil_div(n, 256), 256, 0, s>>>(reinterpret_cast<const float2*>(t->qs), t->leaf_start, t->flags,
+                                                   t->level_off[L], L, npl, S.xh, S.xl, t->skip);
+  ++*nlaunch;
+  TcArgs A;
+  A.img = S.img;
+  A.m2l_off = S.offs;
+  A.m2l_slot = S.slots;
+  A.flags = t->flags;
+  A.level_off = t->level_off_dev;
+  A.Lc = S.out;
+  A.skip = t->skip;
+  A.count = t->near_count;
+  A.box_cells = t->near_count;
+  A.P = npl;
+  A.NA = S.NA;
+  A.Npad = S.Npad;
+  A.lmin = L;
+  A.L = L;
+  A.tgt_set = HFMM_SET_VOL;
+  A.accumulate = 0;
+  for (int l = 0; l <= HFMM_MAX_LEVEL + 1; ++l) A.brick_first[l] = 0;
+  const int h = 1 << (L - 1);
+  const int nb = 8 * (h / BX) * (h / BY) * (h / (NBRK * BZ));
+  A.brick_first[L] = 0;
+  A.brick_first[L + 1] = nb;
+  const int nsplit = std::max(1, std::min(TC_NEAR_SPLIT, (2 * 152 + nb - 1) / nb));
+  A.part = nsplit > 1 ? S.part : nullptr;
+  A.part_stride = (t->level_off[L] + nleaf) * (int64_t)twoP;
+  const size_t stage_bytes = 2 * (size_t)(NBRK * BX * BY * BZ * 128) + 2 * (size_t)S.Npad * 128;
+  const size_t smem = TC_NSTG * stage_bytes + 1024;
+  HFMM_TRY(set_smem_any((const void*)k_m2l_tc, smem));
+  k_m2l_tc<<<dim3(nb, nsplit), TC_THREADS, smem, s>>>(S.maps, A);
+  ++*nlaunch;
+  if (nsplit > 1) {
+    k_tc_reduce<<<ceil_div(nleaf * twoP, 256), 256, 0, s>>>(A.part, A.part_stride, nsplit, t->flags, t->level_off[L],
+                                                           nleaf, twoP, HFMM_SET_VOL, 0, A.Lc, t->skip);
+    ++*nlaunch;
+  }
+  const float2 sig = make_float2((float)t->sigma_vol.x, (float)t->sigma_vol.y);
+  k_tc_near_add<<<ceil_div(nleaf * npl, 256), 256, 0, s>>>(S.out, t->level_off[L], t->leaf_start, t->flags, nleaf, npl,
+                                                           sig, reinterpret_cast<const float2*>(t->qs),
+                                                           reinterpret_cast<float2*>(t->phis), t->skip);
+  ++*nlaunch;
+  return hfmm_last_launch();
 }

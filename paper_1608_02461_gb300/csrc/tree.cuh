@@ -15,6 +15,7 @@ struct DevBuf {
 struct fmm_tree_ext;  // solver workspaces (capi.cu)
 struct fmm_tc_state;  // tensor-core M2L state (m2l_tc.cu)
 struct bnd_op_state;  // boundary -> boundary apply as one kernel (bnd_op.cu)
+struct fmm_tc_near_state;  // volume near field on the tensor cores (m2l_tc.cu)
 
 // kernels launched by the library (all handles)
 void count_launches(int64_t n);
@@ -233,6 +234,12 @@ struct fmm_tree {
   //      use; use_m2l_tcore: 0 off, 1 passes with volume targets, 2 all passes
   fmm_tc_state* m2l_tcore = nullptr;
   int use_m2l_tcore = 1;
+  // ---- volume -> volume near field on the tensor cores (FP32 form, regular
+  //      lattice trees of depth >= 4: every leaf the same block of nodes, so
+  //      the block between two leaves depends only on their offset); set up on
+  //      first use; use_near_tcore 0: always the lattice near-field kernel
+  fmm_tc_near_state* near_tcore = nullptr;
+  int use_near_tcore = 1;
 
   // ---- near field concurrent with the far field: P2P runs on its own
   //      stream (fork/join through events, also inside captured graphs) into
@@ -363,6 +370,11 @@ int m2l_tc_lmin(const fmm_tree* t);
 int m2l_tc_stage(fmm_tree* t, int src_set, int tgt_set, int accumulate, cudaStream_t s, int* nlaunch);
 int m2l_tc_error(cudaStream_t s, bool clear);
 void m2l_tc_release(fmm_tree* t);
+// m2l_tc.cu: the volume -> volume near field (and volume self terms) added to
+// phis on the tensor cores, for passes with volume targets only
+bool near_tc_usable(fmm_tree* t, int src_set, int tgt_set, cudaStream_t s);
+int near_tc_stage(fmm_tree* t, cudaStream_t s, int* nlaunch);
+void near_tc_release(fmm_tree* t);
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, double2* phi_bnd, cudaStream_t s);
 int fmm_scatter(fmm_tree* t, int tgt_set, double2* phi_vol, float2* phi_bnd, cudaStream_t s);
 int fmm_scatter_from(fmm_tree* t, const void* sorted, int tgt_set, double2* phi_vol, double2* phi_bnd,
