@@ -398,30 +398,31 @@ __global__ void k_tc_near_ops(const float2* __restrict__ tab, const int* __restr
 }
 
 // X_hi / X_lo of the leaf level from the sorted weights: the row of leaf m is
-// its npl volume weights (2 npl reals), zero for leaves without volume points
+// its npl volume weights (2 npl reals, padded with zeros to xs reals, a
+// multiple of 4 for the tensor map's row stride), zero for leaves without
+// volume points
 __global__ void k_tc_near_split(const float2* __restrict__ qs, const int* __restrict__ leaf_start,
-                                const int* __restrict__ flags, int64_t off, int l, int npl,
+                                const int* __restrict__ flags, int64_t off, int l, int npl, int xs,
                                 float* __restrict__ xh, float* __restrict__ xl, const int* skip) {
   if (skip && *skip) return;
   const int64_t ncell = (int64_t)1 << (3 * l);
-  const int twoP = 2 * npl;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= ncell * twoP) return;
-  const int64_t m = e / twoP;
-  const int k = (int)(e - m * twoP);
+  if (e >= ncell * xs) return;
+  const int64_t m = e / xs;
+  const int k = (int)(e - m * xs);
   int ix, iy, iz;
   morton_decode((uint64_t)m, ix, iy, iz);
   const int h = 1 << (l - 1);
   const int c = (ix & 1) | ((iy & 1) << 1) | ((iz & 1) << 2);
   const int64_t row = (((int64_t)c * h + (iz >> 1)) * h + (iy >> 1)) * h + (ix >> 1);
   float v = 0.f;
-  if (flags[off + m] & HFMM_SET_VOL) {
+  if (k < 2 * npl && (flags[off + m] & HFMM_SET_VOL)) {
     const float2 q = qs[leaf_start[m] + (k >> 1)];
     v = (k & 1) ? q.y : q.x;
   }
   const float hv = tf32_hi(v);
-  xh[row * twoP + k] = hv;
-  xl[row * twoP + k] = v - hv;
+  xh[row * xs + k] = hv;
+  xl[row * xs + k] = v - hv;
 }
 
 // phis += near field + self term, for the volume points of every leaf
@@ -606,6 +607,7 @@ int m2l_tc_error(cudaStream_t s, bool clear) {
 struct fmm_tc_near_state {
   int ok = 0;        // 1 usable, -1 not for this tree
   int npl = 0, NA = 0, Npad = 0;
+  int xs = 0;        // reals per row of the weight lattices (2 npl rounded up to 4)
   float* img = nullptr;
   float* xh = nullptr;
   float* xl = nullptr;
@@ -670,6 +672,7 @@ static int near_tc_prepare(fmm_tree* t, cudaStream_t s) {
   }
   S->npl = npl;
   const int twoP = 2 * npl;
+  S->xs = (twoP + 3) & ~3;
   S->NA = (twoP + 31) / 32;
   S->Npad = (twoP + 15) / 16 * 16;
   const int nslot = t->near_count;
@@ -694,13 +697,13 @@ static int near_tc_prepare(fmm_tree* t, cudaStream_t s) {
   count_launches(1);
   HFMM_TRY(hfmm_last_launch());
   const int64_t rows = t->level_off[L] + nleaf;
-  HFMM_TRY(tree_alloc(t, (void**)&S->xh, sizeof(float) * nleaf * twoP));
-  HFMM_TRY(tree_alloc(t, (void**)&S->xl, sizeof(float) * nleaf * twoP));
+  HFMM_TRY(tree_alloc(t, (void**)&S->xh, sizeof(float) * nleaf * S->xs));
+  HFMM_TRY(tree_alloc(t, (void**)&S->xl, sizeof(float) * nleaf * S->xs));
   HFMM_TRY(tree_alloc(t, (void**)&S->out, sizeof(float) * rows * twoP));
   HFMM_TRY(tree_alloc(t, (void**)&S->part, sizeof(float) * rows * twoP * TC_NEAR_SPLIT));
   const cuuint64_t hh = (cuuint64_t)half;
-  const cuuint64_t dims[5] = {(cuuint64_t)twoP, hh, hh, hh, 8};
-  const cuuint64_t row = (cuuint64_t)twoP * sizeof(float);
+  const cuuint64_t dims[5] = {(cuuint64_t)S->xs, hh, hh, hh, 8};
+  const cuuint64_t row = (cuuint64_t)S->xs * sizeof(float);
   const cuuint64_t strides[4] = {row, row * hh, row * hh * hh, row * hh * hh * hh};
   const cuuint32_t box[5] = {32, BX, BY, NBRK * BZ, 1};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
@@ -739,9 +742,9 @@ int near_tc_stage(fmm_tree* t, cudaStream_t s, int* nlaunch) {
   fmm_tc_near_state& S = *t->near_tcore;
   const int L = t->L, npl = S.npl, twoP = 2 * npl;
   const int64_t nleaf = (int64_t)1 << (3 * L);
-  const int64_t n = nleaf * twoP;
+  const int64_t n = nleaf * S.xs;
   k_tc_near_split<<<ceil_div(n, 256), 256, 0, s>>>(reinterpret_cast<const float2*>(t->qs), t->leaf_start, t->flags,
-                                                   t->level_off[L], L, npl, S.xh, S.xl, t->skip);
+                                                   t->level_off[L], L, npl, S.xs, S.xh, S.xl, t->skip);
   ++*nlaunch;
   TcArgs A;
   A.img = S.img;
