@@ -194,6 +194,13 @@ void fmm_destroy_tree(fmm_tree* tree);
  *                     (overwritten); a set not on that side may be NULL
  * The adjoint and derivative operators are built on the first call in those
  * modes (device memory held by the handle).
+ * FP32 form: the M2L of levels >= 4 with volume targets runs on the tensor
+ * cores (three TF32 products per product, FP32 accumulation), and on a
+ * regular lattice tree (n divisible by 2^L, every leaf the same block of
+ * nodes) so does the volume sources' near field of an HFMM_FWD apply with
+ * tgt_set = HFMM_SET_VOL (the block between two leaves depends only on their
+ * offset); environment HFMM_M2L_TC=0 / HFMM_NEAR_TC=0 at tree build keeps
+ * the CUDA-core kernels.
  * Errors: INVALID_ARG, NOMEM, CUDA.
  */
 int fmm_apply(fmm_tree* tree, int src_set, int tgt_set,
