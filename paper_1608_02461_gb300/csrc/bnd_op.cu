@@ -1102,6 +1102,9 @@ __device__ void bo_cycle(const BoArgs<T, IO>& A, BoCta<T>& S) {
   __shared__ C<T> snsm[BO_MAX_M];
   __shared__ double hs[2];
   __shared__ int done_s;
+  __shared__ int one_pass_s;
+  bool analytic = false;    // the next step's norm is the one-pass value (no pass C)
+  double next_norm2 = 0.0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = A.nb;
   const int lo = (int)((int64_t)nb * blockIdx.x / gridDim.x), hi = (int)((int64_t)nb * (blockIdx.x + 1) / gridDim.x);
@@ -1126,7 +1129,7 @@ __device__ void bo_cycle(const BoArgs<T, IO>& A, BoCta<T>& S) {
     // the norm of w (||b|| at j = 0): v_j = w / norm on this slice, and (CTA
     // 0) the Arnoldi update of column j - 1 or the start of the cycle
     if (warp == 0) {
-      const double2 s2 = bo_sum_part(pC, 0, gridDim.x, lane);
+      const double2 s2 = analytic ? make_double2(next_norm2, 0.0) : bo_sum_part(pC, 0, gridDim.x, lane);
       if (lane == 0) {
         hs[0] = sqrt(s2.x);
         hs[1] = j > 0 && blockIdx.x == 0 ? sqrt(__ldcg(&A.dots[2 * (m + 1)]).x) : 0.0;
@@ -1161,16 +1164,40 @@ __device__ void bo_cycle(const BoArgs<T, IO>& A, BoCta<T>& S) {
     if (threadIdx.x == 0) done_s = __ldcg(&A.cflags[0]);
     __syncthreads();
     if (done_s) break;
-    // classical Gram-Schmidt, twice: d1 = V^H w, w -= V d1, d2 = V^H w,
-    // w -= V d2, then ||w||^2 (and ||w||^2 before the projections, for the
-    // breakdown test)
+    // classical Gram-Schmidt with the reorthogonalization test of Daniel,
+    // Gragg, Kaufman and Stewart: d1 = V^H w, w -= V d1; with V orthonormal
+    // ||w||^2 = ||w0||^2 - |d1|^2, and when that keeps more than half of
+    // ||w0||^2 one pass is enough (that norm serves the next step);
+    // otherwise d2 = V^H w, w -= V d2 and ||w||^2 summed again.  The test is
+    // taken on sums every CTA forms in the same order, so all agree.
+    // ||w0||^2 also serves the breakdown test.
     bo_slice_dots<T, IO>(A, pA, j + 1, true, lo, hi);
     if (!bo_grid_sync(A.bar, S.gen)) return;
     if (warp == 0) {
       const double2 s2 = bo_sum_part(pA, j + 1, gridDim.x, lane);
-      if (lane == 0 && blockIdx.x == 0) A.dots[2 * (m + 1)] = s2;
+      if (lane == 0) {
+        hs[0] = s2.x;
+        if (blockIdx.x == 0) A.dots[2 * (m + 1)] = s2;
+      }
     }
     bo_slice_project<T, IO>(A, pA, j + 1, dsm, 0, lo, hi);
+    if (threadIdx.x == 0) {
+      double d2sum = 0.0;
+      for (int k = 0; k <= j; ++k) d2sum += dsm[k].x * dsm[k].x + dsm[k].y * dsm[k].y;
+      const double w1 = hs[0] - d2sum;
+      one_pass_s = (w1 > 0.5 * hs[0]) ? 1 : 0;
+      hs[1] = w1;
+    }
+    __syncthreads();
+    if (one_pass_s) {
+      if (blockIdx.x == 0)
+        for (int k = threadIdx.x; k <= j; k += blockDim.x) A.dots[(m + 1) + k] = make_double2(0.0, 0.0);
+      analytic = true;
+      next_norm2 = hs[1];
+      if (!bo_grid_sync(A.bar, S.gen)) return;
+      continue;
+    }
+    analytic = false;
     bo_slice_dots<T, IO>(A, pB, j + 1, false, lo, hi);
     if (!bo_grid_sync(A.bar, S.gen)) return;
     bo_slice_project<T, IO>(A, pB, j + 1, dsm, m + 1, lo, hi);
