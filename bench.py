@@ -64,7 +64,7 @@ P2P_DRAM_BYTES = {"A": 2617088, "B": 520704, "C": 5694976}
 # The boundary operator's kernel (k_bnd_op, one launch = one inner GMRES
 # cycle): dram__bytes_read.sum + dram__bytes_write.sum of one such launch in
 # the benchmark solve (ncu, 64^3 k=16 p=6 FP32, 20 steps), and its steps
-BND_DRAM_BYTES = 280226560
+BND_DRAM_BYTES = 264148224
 # pass C's volume near field runs on the tensor cores in the FP32 form
 # (several launches), so the per-launch near-field counters above do not apply
 NEAR_TC_IN_STAGE = True
