@@ -447,6 +447,62 @@ int fmm_set_timing(fmm_tree* tree, int stage_mask);
 int hfmm_pipe_peaks(double* out, void* stream);
 
 /*
+ * Partition of one FMM apply across ranks (host only: these two calls make
+ * no CUDA call and run without a GPU).
+ *
+ * The octree of Sec. 5.1.1 is cut along the Morton curve of its leaf level
+ * into one contiguous range of leaves per rank, the domain decomposition of
+ * the paper's distributed runs (Sec. 7).  Leaves are addressed by Morton code
+ * m in [0, 8^L): bit 3i of m is bit i of the leaf's x index, bit 3i+1 of y,
+ * bit 3i+2 of z; the leaf of a point x is floor(x 2^L) per axis, clamped to
+ * 2^L - 1; L is the tree depth of fmm_build_tree (the smallest L >= 2 with
+ * leaf_size 8^L >= n_vol).  A cell of level l holds the leaves m with
+ * m >> 3(L - l) equal to its own Morton code.
+ *
+ * hfmm_partition_ranges -- contiguous Morton ranges balanced by cost.
+ *   L            leaf level, 2 <= L <= 8
+ *   leaf_cost    8^L non-negative finite costs in Morton order (host), or
+ *                NULL for equal costs (all-zero costs count as equal)
+ *   nranks       1 <= nranks <= 8^L
+ *   leaf_begin   nranks + 1 int64 (host, written): rank r owns the leaves
+ *                leaf_begin[r] <= m < leaf_begin[r + 1]; every range holds at
+ *                least one leaf, and rank r starts where the running cost is
+ *                closest to r / nranks of the total
+ *
+ * hfmm_partition_let -- the locally essential tree (LET) of one rank: what it
+ * needs from the other ranks for one apply whose targets lie in the leaves
+ * flagged by leaf_tgt and whose sources lie in the leaves flagged by leaf_src.
+ *   L, theta     the tree's depth and separation parameter (0 < theta <= 0.55;
+ *                the lists are the library's own near and M2L lists)
+ *   nranks, leaf_begin, rank   a partition (leaf_begin[0] = 0,
+ *                non-decreasing, leaf_begin[nranks] = 8^L; empty ranges are
+ *                allowed) and the rank, 0 <= rank < nranks
+ *   leaf_tgt, leaf_src   8^L flags in Morton order (host, nonzero = holds
+ *                targets / sources), or NULL for all leaves
+ *   near_leaves  (host, written) ascending Morton codes of the leaves of
+ *                other ranks that hold sources and lie in the near list
+ *                (P2P, Sec. 5.1.2) of one of the rank's target leaves: their
+ *                source weights travel to the rank
+ *   cells        (host, written) for l = 2..L in turn, the ascending Morton
+ *                codes of the level-l cells in the M2L list of one of the
+ *                rank's target cells that hold a source leaf of another rank:
+ *                every other rank with source leaves in such a cell sends its
+ *                partial multipole of it (multipoles add over sources)
+ *   near_cap, cells_cap  capacities of near_leaves and cells (entries)
+ *   n_near       (written) entries of near_leaves
+ *   cell_count   L + 1 int64 (written): cells of level l at cell_count[l]
+ *                (entries 0 and 1 are zero)
+ * near_leaves and cells both NULL: only the counts are written (a size
+ * query).  Otherwise both must be given with capacity for every entry, else
+ * HFMM_ERR_INVALID_ARG and nothing is written.
+ */
+int hfmm_partition_ranges(int L, const double* leaf_cost, int nranks, int64_t* leaf_begin);
+int hfmm_partition_let(int L, double theta, int nranks, const int64_t* leaf_begin, int rank,
+                       const uint8_t* leaf_tgt, const uint8_t* leaf_src, int64_t* near_leaves,
+                       int64_t near_cap, int64_t* n_near, int64_t* cells, int64_t cells_cap,
+                       int64_t* cell_count);
+
+/*
  * hfmm_direct_sum_noalloc -- allocation-free direct Helmholtz sum.
  *
  * The paper has no counterpart to this entry point.  It exists for callers

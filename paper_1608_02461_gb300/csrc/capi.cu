@@ -134,21 +134,6 @@ static void prec_graph_drop(PrecGraph& G) {
 
 namespace {
 
-// theta as a rational num/den with den <= 1000 (exact for decimal inputs)
-void theta_rational(double th, int64_t& num, int64_t& den) {
-  for (int64_t d = 1; d <= 1000; ++d) {
-    double n = th * d;
-    int64_t r = (int64_t)llround(n);
-    if (r > 0 && fabs(n - r) < 1e-9 * d) {
-      num = r;
-      den = d;
-      return;
-    }
-  }
-  den = 1000;
-  num = (int64_t)llround(th * 1000);
-}
-
 void release(fmm_tree* t) {
   if (!t) return;
   for (auto& b : t->bufs) cudaFree(b.ptr);

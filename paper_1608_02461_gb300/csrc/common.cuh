@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "../../include/hfmm.h"
 
 #define HFMM_MAX_P 16
@@ -82,6 +84,32 @@ __host__ __device__ __forceinline__ void morton_decode(uint64_t m, int& ix, int&
   ix = (int)compact3(m);
   iy = (int)compact3(m >> 1);
   iz = (int)compact3(m >> 2);
+}
+
+// ---------------------------------------------------------------- tree lists
+// Two cells of one level whose centres lie d cell widths apart (d2 = |d|^2)
+// are well separated iff theta^2 d2 > 1, theta = num / den (the multipole
+// acceptance test of the octree, Sec. 5.1.1 with theta of Sec. 7).
+__host__ __device__ __forceinline__ bool separated(int d2, int64_t num, int64_t den) {
+  return num * num * (int64_t)d2 > den * den;
+}
+// floor(x / 2) for any sign: the parent offset of a child offset
+__host__ __device__ __forceinline__ int floor_half(int x) { return x >= 0 ? x / 2 : -((1 - x) / 2); }
+
+// theta as a rational num / den (smallest den <= 1000 that represents it to
+// 1e-9), so that the separation test is exact integer arithmetic
+inline void theta_rational(double th, int64_t& num, int64_t& den) {
+  for (int64_t d = 1; d <= 1000; ++d) {
+    double n = th * d;
+    int64_t r = (int64_t)llround(n);
+    if (r > 0 && fabs(n - r) < 1e-9 * d) {
+      num = r;
+      den = d;
+      return;
+    }
+  }
+  den = 1000;
+  num = (int64_t)llround(th * 1000);
 }
 
 // ---------------------------------------------------------------- error plumbing

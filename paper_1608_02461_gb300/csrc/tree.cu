@@ -156,10 +156,6 @@ __global__ void k_parent_flags(const int* child_flags, int ncells, int* flags) {
 
 // ---- lists
 
-__device__ __forceinline__ bool separated(int d2, int64_t num, int64_t den) {
-  return num * num * (int64_t)d2 > den * den;
-}
-__device__ __forceinline__ int floor_half(int x) { return x >= 0 ? x / 2 : -((1 - x) / 2); }
 __device__ __forceinline__ int pack_off(int dx, int dy, int dz) {
   return (dx + 128) | ((dy + 128) << 8) | ((dz + 128) << 16);
 }

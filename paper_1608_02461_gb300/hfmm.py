@@ -11,6 +11,8 @@ import ctypes
 import os
 from dataclasses import dataclass
 
+import numpy as np
+
 HFMM_OK = 0
 HFMM_ERR_INVALID_ARG = -1
 HFMM_ERR_CUDA = -2
@@ -108,6 +110,11 @@ SIGNATURES = {
                                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_double,
                                                ctypes.c_void_p, ctypes.c_void_p]),
     "hfmm_pipe_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "hfmm_partition_ranges": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "hfmm_partition_let": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p]),
 }
 
 # order of hfmm_pipe_peaks' outputs
@@ -406,6 +413,58 @@ def order_for_k(k: float, p_min: int) -> int:
     if st < 1:
         raise HfmmError(st, "hfmm_order_for_k")
     return st
+
+
+def _host_array(a, dtype, n, name):
+    """A contiguous host numpy array of `dtype` with n entries (or None)."""
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if a.shape != (n,):
+        raise ValueError(f"{name}: expected {n} entries, got shape {a.shape}")
+    return a
+
+
+def _aptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def partition_ranges(L: int, nranks: int, leaf_cost=None):
+    """hfmm_partition_ranges: contiguous Morton leaf ranges, one per rank,
+    balanced by leaf_cost (8^L entries in Morton order, or None for equal
+    costs).  Returns leaf_begin (nranks + 1 int64)."""
+    nleaf = 1 << (3 * int(L))
+    cost = _host_array(leaf_cost, np.float64, nleaf, "leaf_cost")
+    out = np.zeros(int(nranks) + 1, dtype=np.int64)
+    _check(lib().hfmm_partition_ranges(int(L), _aptr(cost), int(nranks), out.ctypes.data),
+           "hfmm_partition_ranges")
+    return out
+
+
+def partition_let(L: int, theta: float, leaf_begin, rank: int, leaf_tgt=None, leaf_src=None):
+    """hfmm_partition_let: the locally essential tree of `rank` under the
+    partition leaf_begin.  Returns (near_leaves, cells) with near_leaves an
+    int64 array of Morton leaf codes and cells a dict level -> int64 array of
+    Morton cell codes (levels 2..L)."""
+    L = int(L)
+    nleaf = 1 << (3 * L)
+    b = np.ascontiguousarray(leaf_begin, dtype=np.int64)
+    tg = _host_array(leaf_tgt, np.uint8, nleaf, "leaf_tgt")
+    sr = _host_array(leaf_src, np.uint8, nleaf, "leaf_src")
+    n_near = ctypes.c_int64(0)
+    cnt = np.zeros(L + 1, dtype=np.int64)
+    f = lib().hfmm_partition_let
+    args = (L, float(theta), len(b) - 1, b.ctypes.data, int(rank), _aptr(tg), _aptr(sr))
+    _check(f(*args, None, 0, ctypes.byref(n_near), None, 0, cnt.ctypes.data), "hfmm_partition_let")
+    near = np.zeros(max(n_near.value, 1), dtype=np.int64)
+    cells = np.zeros(max(int(cnt.sum()), 1), dtype=np.int64)
+    _check(f(*args, near.ctypes.data, len(near), ctypes.byref(n_near), cells.ctypes.data, len(cells),
+             cnt.ctypes.data), "hfmm_partition_let")
+    out, c0 = {}, 0
+    for l in range(2, L + 1):
+        out[l] = cells[c0:c0 + cnt[l]].copy()
+        c0 += cnt[l]
+    return near[:n_near.value].copy(), out
 
 
 def check_noalloc_args(src_xyz, q, tgt_xyz, phi, require_cuda=True):

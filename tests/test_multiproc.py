@@ -37,7 +37,7 @@ def _worker(rank, world, port, out):
 def test_barrier_max_over_two_gloo_ranks():
     import torch.multiprocessing as mp
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     assert out[0] == 3.0 and out[1] == 3.0
