@@ -53,7 +53,7 @@ extern "C" int fmm_autotune(fmm_tree* t, void* stream) {
                             {HFMM_SET_BND, HFMM_SET_BND},
                             {HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL},
                             {HFMM_SET_VOL | HFMM_SET_BND, HFMM_SET_VOL | HFMM_SET_BND}};
-  const int fills[4] = {1, 2, 4, 8};
+  const int fills[5] = {1, 2, 4, 8, 16};
   const bool timer_was_on = t->timer.on;
   t->timer.on = false;
   for (const auto& ps : passes) {

@@ -1341,7 +1341,7 @@ int launch_m2l_tma_rt(fmm_tree* t, const FmmDev<T>& d, const C<T>* ops, int src_
   const int variant = t->tuned_variant[tci] >= 0 ? t->tuned_variant[tci] : t->m2l_variant;
   const int fill = t->tuned_variant[tci] >= 0 ? t->tuned_fill[tci] : t->m2l_fill;
   int nsplit = (fill * 152 + nt - 1) / nt;
-  if (nsplit > std::min(8, t->m2l_part_max)) nsplit = std::min(8, t->m2l_part_max);  // CUDA-core pipelines: <= 8
+  if (nsplit > t->m2l_part_max) nsplit = t->m2l_part_max;
   if (nsplit < 1) nsplit = 1;
   C<T>* part = nsplit > 1 ? reinterpret_cast<C<T>*>(t->m2l_part) : nullptr;
   const int64_t pstride = t->total_cells * (int64_t)P;
