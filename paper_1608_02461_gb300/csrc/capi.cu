@@ -218,7 +218,9 @@ static int build_impl(fmm_tree* t, const double* d_vol, const double* d_bnd, cud
   HFMM_TRY(tree_alloc(t, &t->phis, csz * N));
   HFMM_TRY(tree_alloc(t, &t->zero_row, csz * (P + 2)));
   HFMM_CUDA_TRY(cudaMemsetAsync(t->zero_row, 0, csz * (P + 2), s));
-  t->m2l_part_max = 16;  // partial-sum buffers of split offset lists (tensor-core M2L: up to 16)
+  // partial-sum buffers of split offset lists: 32 parts where they take at
+  // most 256 MB, else 16 (the tensor-core M2L splits into at most 16)
+  t->m2l_part_max = csz * t->total_cells * P * 32 <= ((size_t)256 << 20) ? 32 : 16;
   // M2L pipeline: the warp-specialised form wins once the operator is large
   // (p >= 8), the block-synchronous two-stage form below that (measured)
   t->m2l_variant = P >= 64 ? 1 : 0;

@@ -570,7 +570,7 @@ int m2l_tc_stage(fmm_tree* t, int src_set, int tgt_set, int accumulate, cudaStre
   }
   A.brick_first[L + 1] = nb;
   // split the offset lists until the grid covers the GPU about twice
-  const int nsplit = std::max(1, std::min(t->m2l_part_max, (2 * 152 + nb - 1) / nb));
+  const int nsplit = std::max(1, std::min(std::min(t->m2l_part_max, 16), (2 * 152 + nb - 1) / nb));
   A.part = nsplit > 1 ? reinterpret_cast<float*>(t->m2l_part) : nullptr;
   A.part_stride = t->total_cells * (int64_t)twoP;
   const size_t stage_bytes = 2 * (size_t)(NBRK * BX * BY * BZ * 128) + 2 * (size_t)S.Npad * 128;
