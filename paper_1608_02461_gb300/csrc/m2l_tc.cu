@@ -570,7 +570,7 @@ int m2l_tc_stage(fmm_tree* t, int src_set, int tgt_set, int accumulate, cudaStre
   }
   A.brick_first[L + 1] = nb;
   // split the offset lists until the grid covers the GPU about twice
-  const int nsplit = std::max(1, std::min(std::min(t->m2l_part_max, 16), (2 * 152 + nb - 1) / nb));
+  const int nsplit = std::max(1, std::min(t->m2l_part_max, (2 * 152 + nb - 1) / nb));
   A.part = nsplit > 1 ? reinterpret_cast<float*>(t->m2l_part) : nullptr;
   A.part_stride = t->total_cells * (int64_t)twoP;
   const size_t stage_bytes = 2 * (size_t)(NBRK * BX * BY * BZ * 128) + 2 * (size_t)S.Npad * 128;
@@ -612,14 +612,21 @@ struct fmm_tc_near_state {
   float* xh = nullptr;
   float* xl = nullptr;
   float* out = nullptr;   // [level_off[L] + 8^L][2 npl] (rows of the leaf level used)
-  float* part = nullptr;  // [TC_NEAR_SPLIT][level_off[L] + 8^L][2 npl]
+  float* part = nullptr;  // [nsplit][level_off[L] + 8^L][2 npl]
+  int nsplit = 1;         // parts of the offset list (grid about two full waves)
   int* offs = nullptr;    // [8][near_count] packed near offsets (every class the same list)
   int* slots = nullptr;   // [8][near_count] slot = offset index
   TcMaps maps;
 };
 
 namespace {
-constexpr int TC_NEAR_SPLIT = 16;
+constexpr int TC_NEAR_SPLIT = 32;  // at most this many parts of the offset list
+
+// brick pairs of the leaf level
+int near_bricks(int L) {
+  const int h = 1 << (L - 1);
+  return 8 * (h / BX) * (h / BY) * (h / (NBRK * BZ));
+}
 }
 
 void near_tc_release(fmm_tree* t) {
@@ -700,7 +707,11 @@ static int near_tc_prepare(fmm_tree* t, cudaStream_t s) {
   HFMM_TRY(tree_alloc(t, (void**)&S->xh, sizeof(float) * nleaf * S->xs));
   HFMM_TRY(tree_alloc(t, (void**)&S->xl, sizeof(float) * nleaf * S->xs));
   HFMM_TRY(tree_alloc(t, (void**)&S->out, sizeof(float) * rows * twoP));
-  HFMM_TRY(tree_alloc(t, (void**)&S->part, sizeof(float) * rows * twoP * TC_NEAR_SPLIT));
+  {
+    const int nb = near_bricks(L);
+    S->nsplit = std::max(1, std::min(TC_NEAR_SPLIT, (2 * 152 + nb - 1) / nb));
+  }
+  HFMM_TRY(tree_alloc(t, (void**)&S->part, sizeof(float) * rows * twoP * S->nsplit));
   const cuuint64_t hh = (cuuint64_t)half;
   const cuuint64_t dims[5] = {(cuuint64_t)S->xs, hh, hh, hh, 8};
   const cuuint64_t row = (cuuint64_t)S->xs * sizeof(float);
@@ -764,11 +775,10 @@ int near_tc_stage(fmm_tree* t, cudaStream_t s, int* nlaunch) {
   A.tgt_set = HFMM_SET_VOL;
   A.accumulate = 0;
   for (int l = 0; l <= HFMM_MAX_LEVEL + 1; ++l) A.brick_first[l] = 0;
-  const int h = 1 << (L - 1);
-  const int nb = 8 * (h / BX) * (h / BY) * (h / (NBRK * BZ));
+  const int nb = near_bricks(L);
   A.brick_first[L] = 0;
   A.brick_first[L + 1] = nb;
-  const int nsplit = std::max(1, std::min(TC_NEAR_SPLIT, (2 * 152 + nb - 1) / nb));
+  const int nsplit = S.nsplit;
   A.part = nsplit > 1 ? S.part : nullptr;
   A.part_stride = (t->level_off[L] + nleaf) * (int64_t)twoP;
   const size_t stage_bytes = 2 * (size_t)(NBRK * BX * BY * BZ * 128) + 2 * (size_t)S.Npad * 128;
