@@ -386,8 +386,9 @@ int gmres_solve_batched(fmm_tree** trees, const void** d_b, void** d_x, int coun
  * fmm_autotune -- times the M2L kernel variants (two-stage block pipeline,
  * warp-specialised three-stage pipeline, pair lists) and the split of the
  * per-tile offset lists (grid filled to 1, 2, 4, 8 or 16 x 152 blocks, at
- * most 16 parts per tile) on the
- * FMM passes of the preconditioner and on the full apply, then, with the
+ * most 32 parts per tile, 16 on trees whose 32 partial-sum slots would take
+ * more than 256 MB) on the FMM passes of the preconditioner and on the full
+ * apply, then, with the
  * chosen M2L, the tile shapes of the lattice near field (tiled 4 x 4
  * target-source groups or not in the FP32 form; at most 8, 16 or 32 threads
  * per group of targets; one block per SM or as many as fit) and whether the
