@@ -3,7 +3,9 @@ hfmm_partition_let), on the CPU: the Morton ranges and their balance, the
 locally essential tree against its definition written out on the oracle's own
 near and M2L lists, the size query and argument errors, and a distributed
 apply over gloo ranks (world sizes 2 and 3) that exchanges only what the plan
-lists and reproduces the single-rank oracle apply.  The per-rank arithmetic is
+lists and reproduces the single-rank oracle apply, and the whole preconditioner
+(passes A and C, the inner GMRES over pass B with all-reduced dots) split over
+two ranks against the oracle's.  The per-rank arithmetic is
 the oracle's FMM stages (Sec. 5.1.2); the library supplies the plan alone.
 No GPU is involved."""
 import ctypes
@@ -316,9 +318,9 @@ def _free_port():
     return p
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_distributed_apply_matches_single_rank_oracle(world):
-    torch = pytest.importorskip("torch")
+def _spawn(worker, world):
+    """Run worker(rank, world, port, out) on `world` gloo ranks; returns out."""
+    pytest.importorskip("torch")
     import torch.multiprocessing as mp
     mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
@@ -326,13 +328,19 @@ def test_distributed_apply_matches_single_rank_oracle(world):
     keep = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
     os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
     try:
-        mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        mp.spawn(worker, args=(world, _free_port(), out), nprocs=world, join=True)
     finally:
         for v, x in keep.items():
             if x is None:
                 os.environ.pop(v, None)
             else:
                 os.environ[v] = x
+    return dict(out)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_distributed_apply_matches_single_rank_oracle(world):
+    out = _spawn(_worker, world)
     pr = _problem()
     full_M = sum(8 ** l for l in range(2, pr.fmm.L + 1)) * pr.fmm.P
     for rank in range(world):
@@ -341,3 +349,123 @@ def test_distributed_apply_matches_single_rank_oracle(world):
             assert err < 1e-12, (world, rank, name, err)
             # less than the multipoles of every cell plus every source weight
             assert 0 < words < 2 * (full_M + len(pr.points)), (rank, name, words)
+
+
+# ---------------------------------------------------------------- distributed preconditioner
+
+INNER_STEPS = 8
+
+
+def _dist_dot(u, v, dist, torch):
+    """sum over all ranks of vdot(u, v); each rank's vectors are zero off its own points"""
+    z = np.vdot(u, v)
+    t = torch.tensor([z.real, z.imag], dtype=torch.float64)
+    dist.all_reduce(t)
+    return complex(t[0].item(), t[1].item())
+
+
+def _dist_gmres(A, b, steps, dist, torch):
+    """The oracle's GMRES (readings G1-G6: zero start, modified Gram-Schmidt,
+    complex Givens rotations) for one cycle of `steps` steps, on vectors held
+    in pieces: every inner product and norm is a sum over the ranks
+    (all-reduce), the scalars of the least-squares problem are then the same
+    on every rank.  Returns x and the number of all-reduces."""
+    from oracle.gmres import givens
+    nred = 0
+
+    def dot(u, v):
+        nonlocal nred
+        nred += 1
+        return _dist_dot(u, v, dist, torch)
+
+    beta = np.sqrt(dot(b, b).real)
+    m = steps
+    V = [b / beta]
+    H = np.zeros((m + 1, m), dtype=np.complex128)
+    cs = np.zeros(m)
+    sn = np.zeros(m, dtype=np.complex128)
+    g = np.zeros(m + 1, dtype=np.complex128)
+    g[0] = beta
+    for j in range(m):
+        w = A(V[j])
+        for i in range(j + 1):
+            H[i, j] = dot(V[i], w)
+            w = w - H[i, j] * V[i]
+        hnext = np.sqrt(dot(w, w).real)
+        H[j + 1, j] = hnext
+        for i in range(j):
+            a_, b_ = H[i, j], H[i + 1, j]
+            H[i, j] = cs[i] * a_ + sn[i] * b_
+            H[i + 1, j] = -np.conj(sn[i]) * a_ + cs[i] * b_
+        c, s = givens(H[j, j], H[j + 1, j])
+        cs[j], sn[j] = c, s
+        H[j, j] = c * H[j, j] + s * H[j + 1, j]
+        H[j + 1, j] = 0.0
+        g[j + 1] = -np.conj(s) * g[j]
+        g[j] = c * g[j]
+        V.append(w / hnext)
+    y = np.zeros(m, dtype=np.complex128)
+    for i in range(m - 1, -1, -1):
+        y[i] = (g[i] - H[i, i + 1:m] @ y[i + 1:]) / H[i, i]
+    return sum(y[i] * V[i] for i in range(m)), nred
+
+
+def _precond_worker(rank, world, port, out):
+    """z = M^-1 r (Sec. 5.2-5.3: Pass A, the inner boundary solve, Pass C) with
+    every point owned by the rank of its leaf: the three FMM passes exchange
+    what the plan lists, the inner GMRES all-reduces its dots and norms."""
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        pr = _problem()
+        L = pr.fmm.L
+        leaf = _leaf_of_points(pr)
+        cost = np.bincount(leaf, minlength=8 ** L).astype(np.float64)
+        b = hfmm.partition_ranges(L, world, cost)
+        mine = (np.searchsorted(b, leaf, side="right") - 1) == rank
+        NO, h = pr.NO, pr.h
+        rng = np.random.default_rng(77)
+        r = rng.standard_normal(NO) + 1j * rng.standard_normal(NO)     # every rank draws the same r
+        r_loc = np.where(mine[:NO], r, 0.0)                              # and keeps its own part
+        words = 0
+
+        def apply(q, src, tgt):
+            nonlocal words
+            phi, wd = _distributed_apply(pr, np.where(mine, q, 0.0), src, tgt, b, rank, world, dist, torch)
+            words += wd
+            return phi
+
+        qa = np.zeros(NO + pr.NG, dtype=np.complex128)
+        qa[:NO] = h ** 3 * r_loc
+        g = apply(qa, pr.vol, pr.bnd)[NO:]                                # Pass A
+
+        def V(qb):                                                        # Pass B
+            qq = np.zeros(NO + pr.NG, dtype=np.complex128)
+            qq[NO:] = h ** 2 * qb
+            return apply(qq, pr.bnd, pr.bnd)[NO:]
+
+        q, nred = _dist_gmres(V, -g, INNER_STEPS, dist, torch)
+        qa[NO:] = h ** 2 * q
+        z = apply(qa, pr.vol | pr.bnd, pr.vol)[:NO]                      # Pass C
+        tot = torch.from_numpy(z.view(np.float64).copy())
+        dist.all_reduce(tot)
+        zg = tot.numpy().view(np.complex128)
+        ref, its = pr.precond(r, inner_rtol=1e-15, inner_maxit=INNER_STEPS, inner_m=INNER_STEPS)
+        err = np.linalg.norm(zg - ref) / np.linalg.norm(ref)
+        out[rank] = (float(err), int(its), int(nred), int(words))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_distributed_preconditioner_matches_oracle():
+    out = _spawn(_precond_worker, 2)
+    for rank in range(2):
+        err, its, nred, words = out[rank]
+        assert its == INNER_STEPS
+        assert err < 1e-12, (rank, err)
+        # one dot per Gram-Schmidt coefficient and one norm per step, plus the first norm
+        assert nred == 1 + sum(j + 2 for j in range(INNER_STEPS))
+        assert words > 0
